@@ -1,0 +1,470 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT-based Zernike moment path on one or more GB300s.
+
+Workload: 3840x2160 float32 frames of 32 random anisotropic Gaussian blobs
+(centres area-uniform in the disk, sigma 5-40 px, amplitude 0.2-1) plus noise
+of standard deviation 0.01, the disk of diameter 2160 centred; moments up to
+n_max = 100 on a 1024 x 1024 polar grid.  A step is one pass of the whole hot
+path over a batch of B frames already resident in HBM:
+  ring spectra (bilinear polar resampling + ring real FFT, polar samples kept)
+  -> radial projection (Eq. 1) -> reconstruction on the polar nodes (Eq. 9,
+  Neumann) -> reconstruction errors on the polar nodes (Eq. 10, Eq. 13).
+The FP64 radial-polynomial table (Eq. 7) is built once at plan time, outside
+the timed region, and reported as plan_ms.
+
+Several GPUs run independent replicas (no collective); the value is the images
+of all ranks divided by the slowest rank's time.  ``--impl reference`` times
+the FP64 CPU oracle instead, on bounded ring samples of the same workload.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ZM images/s at 4K n<=100 + p99 latency, mixed-prec vs FP32, err<=1e-4"
+H, W, N_BLOBS = 2160, 3840, 32
+N_MAX, N_RHO, N_THETA = 100, 1024, 1024
+WORKLOAD = "4K blob frames 3840x2160, disk d=2160 centred, n_max=100, N_rho=N_theta=1024, bilinear, midpoint rho"
+SYNTH_WORKLOAD_ID = 2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3", "fp16x3"])
+    ap.add_argument("--quick", action="store_true", help="skip latency / e2e / cpu-baseline extras")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == len(self.FIELDS):
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ---------------------------------------------------------------- workload facts
+def geometry():
+    return (W - 1) / 2.0, (H - 1) / 2.0, min(H, W) / 2.0
+
+
+def touched_sector_bytes():
+    """Distinct 32-byte image sectors that the bilinear stencil of all
+    N_rho x N_theta samples touches (row-major float32 frame, row pitch W)."""
+    cx, cy, r = geometry()
+    rho = (np.arange(N_RHO) + 0.5) / N_RHO
+    th = 2 * np.pi * np.arange(N_THETA) / N_THETA
+    X = cx + r * rho[:, None] * np.cos(th)[None, :]
+    Y = cy - r * rho[:, None] * np.sin(th)[None, :]
+    x0 = np.floor(X).astype(np.int64).ravel()
+    y0 = np.floor(Y).astype(np.int64).ravel()
+    secs = []
+    for dy in (0, 1):
+        for dx in (0, 1):
+            x, y = x0 + dx, y0 + dy
+            ok = (x >= 0) & (x < W) & (y >= 0) & (y < H)
+            secs.append(((y[ok] * W + x[ok]) * 4) // 32)
+    return int(np.unique(np.concatenate(secs)).size) * 32
+
+
+def disk_box_bytes():
+    return min(H, W) * min(H, W) * 4
+
+
+def make_frames(n, start=0):
+    from paper_2304_14492_gb300 import synth
+    return [synth.blob_image(H, W, N_BLOBS, workload=SYNTH_WORKLOAD_ID, index=start + b) for b in range(n)]
+
+
+def read_profile_traffic(kernel_tag):
+    """Per-launch DRAM bytes of `kernel_tag` from the committed ncu summary, if
+    the summary was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_ring_spectra_4k.md")
+    src = os.path.join(ROOT, "paper_2304_14492_gb300", "csrc", "moments.cu")
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None, None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    traffic, src_sha, batch = None, None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_image:"):
+            traffic = float(line.split(":")[1].split()[0])
+        if line.startswith("source_sha:"):
+            src_sha = line.split(":")[1].strip()
+    if src_sha != sha:
+        return None, "kernel changed since the ncu capture"
+    return traffic, None
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_pass(img, ring_idx):
+    """The FP64 oracle on the rings `ring_idx` of one frame: resampling, angular
+    DFT, partial radial projection, reconstruction on those rings, errors."""
+    import oracle
+    rho_all, wr_all = oracle.grid.radial_nodes(N_RHO)
+    rho, wr = rho_all[ring_idx], wr_all[ring_idx]
+    fhat = oracle.resample.polar_resample(img, rho, N_THETA, geometry())
+    F = oracle.moments.angular_dft(fhat, N_MAX)
+    table = oracle.zernike.zrp_table(N_MAX, rho)
+    Z = oracle.moments.project(F, wr, N_THETA, N_MAX, table=table)
+    G = oracle.reconstruct.radial_spectrum(Z, N_MAX, rho, neumann=True)
+    k = np.arange(N_THETA)[None, :]
+    m = np.arange(N_MAX + 1)[:, None]
+    ang = 2 * np.pi * ((m * k) % N_THETA) / N_THETA
+    rec = (G @ (np.cos(ang) + 1j * np.sin(ang))).real
+    d = fhat - rec
+    return Z, float(np.sum(d * d) / np.sum(fhat * fhat))
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def cpu_baseline(budget_s=12.0):
+    """Whole frames through the oracle on the host cores for about budget_s."""
+    img = make_frames(1, start=1000)[0].astype(np.float64)
+    rings = np.arange(N_RHO)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle_pass(img, rings)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 64:
+            break
+    return {"value": n / el, "unit": "images/s", "cores": blas_threads(), "kind": "oracle",
+            "sample": "%d whole 4K frame(s) through the FP64 oracle (moments + polar reconstruction + errors), "
+                      "%.1f s of CPU time, numpy/BLAS on %d host cores" % (n, el, os.cpu_count())}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    img = make_frames(1, start=2000)[0].astype(np.float64)
+    # size the per-step ring sample so that warmup + steps take ~2 minutes
+    t0 = time.perf_counter()
+    oracle_pass(img, np.arange(0, N_RHO, 16))
+    t_per_ring = (time.perf_counter() - t0) / (N_RHO // 16)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n_rings = int(max(1, min(N_RHO, budget / max(t_per_ring, 1e-9))))
+    rng = np.random.default_rng(0)
+    samples = [np.sort(rng.choice(N_RHO, n_rings, replace=False)) for _ in range(args.steps + args.warmup)]
+    for s in samples[:args.warmup]:
+        oracle_pass(img, s)
+    t0 = time.perf_counter()
+    for s in samples[args.warmup:]:
+        oracle_pass(img, s)
+    el = time.perf_counter() - t0
+    frac = args.steps * n_rings / N_RHO            # frames' worth of work done
+    value = frac / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": 1, "sample_rings_per_step": n_rings},
+            "cpu_baseline": {"value": value, "unit": "images/s", "cores": blas_threads(), "kind": "oracle",
+                             "sample": "%d random rings of 1024 per step (1/%0.1f frame), scaled to frames"
+                                       % (n_rings, N_RHO / n_rings)},
+            "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gb300(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2304_14492_gb300 import native as zm
+
+    B = args.batch
+    prec = args.prec
+    if prec == "auto":
+        prec = "fp32"
+    pflag = {"fp32": zm.ZM_PREC_FP32, "bf16x3": zm.ZM_PREC_BF16X3, "fp16x3": zm.ZM_PREC_FP16X3}
+    P = zm.zm_num_moments(N_MAX)
+    frames = make_frames(B, start=rank * B)
+    imgs = torch.from_numpy(np.stack(frames)).to(dev)
+    views = [imgs[b] for b in range(B)]
+    del frames
+
+    t0 = time.perf_counter()
+    try:
+        plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, pflag[prec])
+    except zm.ZmError as e:
+        if e.status != zm.ZM_EUNSUPPORTED:
+            raise
+        prec = "fp32"
+        plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, pflag[prec])
+    plan_ms = 1000 * (time.perf_counter() - t0)
+    plan32 = plan if prec == "fp32" else zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_FP32)
+    zm.zm_plan_reserve(plan, B)
+    zm.zm_plan_reserve(plan32, B)
+
+    st = torch.cuda.current_stream(dev)
+    spectra = torch.empty((N_MAX + 1, B, 2, N_RHO), device=dev)
+    out = torch.empty((B, P, 2), device=dev)
+    fhat = torch.empty((B, N_RHO, N_THETA), device=dev)
+    frec = torch.empty((B, N_RHO, N_THETA), device=dev)
+    err = torch.empty((B, 4), device=dev, dtype=torch.float64)
+
+    def step(kb_events=None):
+        if kb_events is not None:
+            kb_events[0].record(st)
+        zm.zm_ring_spectra(plan, views, spectra, fhat, st)
+        if kb_events is not None:
+            kb_events[1].record(st)
+        zm.zm_project(plan, spectra, B, out, 0, st)
+        zm.zm_reconstruct(plan, out, B, frec, zm.ZM_NEUMANN, st)
+        zm.zm_errors_polar(plan, fhat, frec, B, err, st)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    kb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    l0 = zm.zm_launch_count()
+    ev0.record(st)
+    for k in range(args.steps):
+        step(kb[k])
+    ev1.record(st)
+    torch.cuda.synchronize(dev)
+    l1 = zm.zm_launch_count()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    kb_ms = statistics.mean(a.elapsed_time(b) for a, b in kb)
+    value = world * B * args.steps / (ms / 1000.0)
+
+    # roofline of the dominant kernel (ring spectra): algorithmic bytes per launch
+    sectors = touched_sector_bytes()
+    f_bytes = (N_MAX + 1) * N_RHO * 8
+    fhat_bytes = N_RHO * N_THETA * 4
+    kb_bytes = B * (sectors + f_bytes + fhat_bytes)
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = kb_bytes / (kb_ms / 1000.0) / 1e9
+    traffic, traffic_note = read_profile_traffic("k_ring_spectra")
+    roofline = {"bound": "hbm", "kernel": "k_ring_spectra", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": (traffic * B if traffic else None),
+                "algorithmic_bytes_per_launch": kb_bytes, "launch_ms": kb_ms,
+                "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+                "per_image_bytes": {"touched_sectors": sectors, "spectra_out": f_bytes, "polar_samples_out": fhat_bytes,
+                                    "disk_box": disk_box_bytes()}}
+    if traffic_note:
+        roofline["traffic_note"] = traffic_note
+
+    line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else prec.replace("x3", "x3+f32acc"), "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "global_batch": B * world,
+                       "precision": prec, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (%d MB of frames per step)" % (B * H * W * 4 // 2**20),
+                       "step": "ring spectra + projection + polar reconstruction (Neumann) + polar errors"},
+            "roofline": roofline, "gpu_launches": l1 - l0, "clocks": clocks, "plan_ms": plan_ms}
+
+    if rank == 0 and not args.quick:
+        line.update(extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P))
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+    if plan32 != plan:
+        zm.zm_plan_destroy(plan32)
+    zm.zm_plan_destroy(plan)
+
+
+def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
+    res = {}
+    # moments-only throughput, mixed precision vs FP32 on the same frames
+    def moments_rate(p, reps=50):
+        for _ in range(5):
+            zm.zm_moments(p, views, out, 0, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            zm.zm_moments(p, views, out, 0, st)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        return B * reps / (e0.elapsed_time(e1) / 1000.0)
+
+    res["moments_only_images_per_s"] = {prec: moments_rate(plan)}
+    if plan32 != plan:
+        res["moments_only_images_per_s"]["fp32"] = moments_rate(plan32)
+
+    # error vs the FP64 oracle for every precision, on frame 0
+    import oracle
+    img0 = views[0].double().cpu().numpy()
+    Zref = oracle.moments.moments(img0, N_MAX, N_RHO, N_THETA)
+    errs = {}
+    for name, p in ((prec, plan), ("fp32", plan32)):
+        o1 = torch.empty((1, P, 2), device=dev)
+        zm.zm_moments(p, [views[0]], o1, 0, st)
+        torch.cuda.synchronize(dev)
+        z = o1[0].double().cpu().numpy()
+        errs[name] = oracle.metrics.rel_max_err(z[:, 0] + 1j * z[:, 1], Zref)
+    res["err_vs_fp64"] = errs
+
+    # single-frame latency (L2 flushed between calls)
+    flush = torch.empty(64 * 2**20, device=dev, dtype=torch.float32)     # 256 MB > L2
+    o1 = torch.empty((1, P, 2), device=dev)
+    lat = []
+    for k in range(120):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        zm.zm_moments(plan, [views[k % B]], o1, 0, st)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        if k >= 20:
+            lat.append(e0.elapsed_time(e1))
+    lat.sort()
+    res["latency_b1_ms"] = {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                            "calls": len(lat), "note": "device time of one zm_moments call, cold L2"}
+    del flush
+
+    # end to end through the public API: pinned host frames -> device -> full
+    # step -> moments and errors back to the host
+    host = torch.empty((B, H, W), dtype=torch.float32, pin_memory=True)
+    host.copy_(torch.stack([v for v in views]).cpu())
+    dimg = torch.empty((B, H, W), device=dev)
+    dviews = [dimg[b] for b in range(B)]
+    fh = torch.empty((B, N_RHO, N_THETA), device=dev)
+    fr = torch.empty((B, N_RHO, N_THETA), device=dev)
+    er = torch.empty((B, 4), device=dev, dtype=torch.float64)
+    hout = torch.empty((B, P, 2), dtype=torch.float32, pin_memory=True)
+    herr = torch.empty((B, 4), dtype=torch.float64, pin_memory=True)
+
+    def e2e_step():
+        dimg.copy_(host, non_blocking=True)
+        zm.zm_moments_ex(plan, dviews, out, fh, 0, st)
+        zm.zm_reconstruct(plan, out, B, fr, zm.ZM_NEUMANN, st)
+        zm.zm_errors_polar(plan, fh, fr, B, er, st)
+        hout.copy_(out, non_blocking=True)
+        herr.copy_(er, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    reps = max(5, min(args.steps, 40))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        e2e_step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    res["e2e"] = {"value": B * reps / (e0.elapsed_time(e1) / 1000.0), "unit": "images/s",
+                  "h2d_bytes_per_step": B * H * W * 4, "d2h_bytes_per_step": B * P * 8 + B * 4 * 8,
+                  "steps": reps}
+    return res
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * zm.h - C ABI of the GB300 (sm_103a) FFT-based Zernike moment library.
+ *
+ * Method: M. Al-Rawi, "Ultra-Fast Zernike Moments using FFT and GPU"
+ * (arXiv 2304.14492).  Moments follow Eq. 1 on a polar grid; the radial
+ * polynomials come from the Chebyshev-U / DFT identity of Sec. 2.1 (Eq. 7-8);
+ * reconstruction follows Eq. 9; the Neumann factor is Eq. 14-15; the errors are
+ * Eq. 10 and Eq. 13 (Sec. 2.4); min-max normalisation is the step of Sec. 3 /
+ * Table I.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a status code (ZM_OK = 0 on success) and never
+ *    aborts.  On failure zm_last_error() gives a per-thread detail string.
+ *  - Image, moment and output buffers are DEVICE pointers owned by the caller
+ *    (e.g. the data_ptr() of a CUDA tensor).  The descriptor arrays
+ *    (zm_image_t / zm_canvas_t) are HOST arrays read during the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously on it; results are valid once the stream
+ *    has been synchronised.  A plan may be used from one stream at a time.
+ *  - Geometry: pixel (x = column, y = row) has its centre at integer
+ *    coordinates; the unit disk maps to the circle of centre (cx, cy) and
+ *    radius `radius` pixels; theta runs counter-clockwise with y pointing up,
+ *    so the polar point (rho, theta) sits at X = cx + radius rho cos(theta),
+ *    Y = cy - radius rho sin(theta).  radius <= 0 selects the inscribed,
+ *    centred disk: cx = (W-1)/2, cy = (H-1)/2, radius = min(H, W)/2.
+ *  - Polar grid: theta_k = 2 pi k / N_theta; rho_i = (i + 1/2) / N_rho
+ *    (midpoint rule, default) or the Gauss-Legendre nodes on [0, 1].  Image
+ *    values are sampled bilinearly, neighbours outside the image count as 0.
+ *  - Moment layout: for each image, P(n_max) complex values as interleaved
+ *    float pairs (re, im), in the order n = 0..n_max, then m = n mod 2, ..., n
+ *    step 2 (only m >= 0 is stored; Z_{n,-m} = conj(Z_nm), Sec. 2).  The index
+ *    of (n, m) is zm_index(n, m); P(n_max) = zm_num_moments(n_max).
+ */
+#ifndef ZM_H
+#define ZM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ZM_OK            0
+#define ZM_EINVAL        1  /* bad argument: sizes, flags, null pointer      */
+#define ZM_ENOMEM        2  /* device allocation failed or budget exceeded   */
+#define ZM_ECUDA         3  /* CUDA launch / API error (detail kept)         */
+#define ZM_ETIMEOUT      4  /* a bounded wait ran out                        */
+#define ZM_EUNSUPPORTED  5  /* valid request this build does not implement   */
+
+/* ---- plan flags (zm_plan) ---------------------------------------------- */
+#define ZM_GRID_MIDPOINT 0x0u   /* rho_i = (i + 1/2)/N_rho, weight rho_i/N_rho */
+#define ZM_GRID_GAUSS    0x1u   /* Gauss-Legendre nodes and weights on [0, 1]  */
+#define ZM_PREC_FP32     0x00u  /* radial projection in FP32 (CUDA cores)      */
+#define ZM_PREC_BF16X3   0x10u  /* projection on tensor cores, bf16 hi+lo split */
+#define ZM_PREC_FP16X3   0x20u  /* projection on tensor cores, fp16 hi+lo split */
+
+/* ---- call flags --------------------------------------------------------- */
+#define ZM_NEUMANN       0x1u   /* see zm_moments / zm_reconstruct            */
+
+typedef struct zm_plan_s* zm_plan_t;
+
+/* A read-only device image.  Row y starts at data + y * pitch (elements). */
+typedef struct {
+    const float* data;
+    int height, width;
+    long long pitch;
+    float cx, cy, radius;
+} zm_image_t;
+
+/* A writable device image of the same layout (reconstruction target). */
+typedef struct {
+    float* data;
+    int height, width;
+    long long pitch;
+    float cx, cy, radius;
+} zm_canvas_t;
+
+/* ---- index set (D5 layout; Sec. 2, Eq. 1 conditions) -------------------- */
+
+/* P(n_max): number of stored moments with n <= n_max; -1 if n_max < 0. */
+int zm_num_moments(int n_max);
+
+/* Position of (n, m) in a moment vector; -1 unless 0 <= m <= n, n-m even. */
+int zm_index(int n, int m);
+
+/* Static text for a status code. */
+const char* zm_strerror(int status);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char* zm_last_error(void);
+
+/* ---- plans (Sec. 2.1, Eq. 7-8) ------------------------------------------- */
+
+/*
+ * Create a plan for moments up to order n_max on an N_rho x N_theta polar grid.
+ * Builds, on the current CUDA device, the FP64 table R_nm(rho_i) with Eq. 7
+ * (the DFT over k of U_n(rho cos(2 pi k / N_z)) with N_z the next power of two
+ * >= max(8, 2 n_max + 2), so N_z > n + m always), the projection operands
+ * derived from it, and the angular tables.  Synchronous; allocates device
+ * memory.  FP64 tables are cached per (device, grid, N_rho) and shared by plans
+ * of any n_max up to the largest built so far.
+ *  n_max   >= 0
+ *  n_rho   in [1, 65536]
+ *  n_theta a power of two in [8, 2048] with n_theta >= 2 n_max + 1
+ *  flags   one ZM_GRID_* | one ZM_PREC_*
+ * Errors: ZM_EINVAL, ZM_ENOMEM, ZM_ECUDA, ZM_EUNSUPPORTED.
+ */
+int zm_plan(zm_plan_t* plan, int n_max, int n_rho, int n_theta, unsigned flags);
+
+/* Release the plan and its workspace (waits for the device). NULL is ok. */
+int zm_plan_destroy(zm_plan_t plan);
+
+/* Grow the plan's workspace so that later calls with batch <= `batch`
+ * allocate nothing (e.g. before CUDA graph capture).  Synchronous. */
+int zm_plan_reserve(zm_plan_t plan, int batch);
+
+/* Plan parameters; any output pointer may be NULL. */
+int zm_plan_info(zm_plan_t plan, int* n_max, int* n_rho, int* n_theta,
+                 int* num_moments, unsigned* flags);
+
+/* Copy the FP64 table R_nm(rho_i), shape [P(n_max)][N_rho] in moment order,
+ * to device buffer `dst` (Eq. 7 output).  Asynchronous on `stream`. */
+int zm_plan_table(zm_plan_t plan, double* dst, void* stream);
+
+/* Copy the radial nodes rho_i and radial weights wr_i (the Jacobian rho
+ * included: sum_i wr_i g(rho_i) approximates the integral of g(rho) rho over
+ * [0, 1]) to device buffers of N_rho doubles.  Either may be NULL. */
+int zm_plan_nodes(zm_plan_t plan, double* rho, double* wr, void* stream);
+
+/* ---- moments (Eq. 1, Eq. 14-15) ------------------------------------------ */
+
+/*
+ * Zernike moments of `batch` images: bilinear polar resampling, a real FFT of
+ * every ring, and the radial projection
+ *     Z_nm = (n+1)/pi * sum_i wr_i (2 pi / N_theta) R_nm(rho_i) F_m(rho_i),
+ * F_m(rho_i) = sum_k f(rho_i, theta_k) e^{-j m theta_k}.
+ *  imgs  host array of `batch` device image descriptors (any sizes)
+ *  out   device float[batch][P][2]
+ *  flags ZM_NEUMANN divides each moment by eps_m (2 for m = 0, else 1; Eq. 14)
+ * Errors: ZM_EINVAL (batch < 1, null pointers, image < 1x1, bad pitch),
+ * ZM_ENOMEM (workspace growth), ZM_ECUDA.
+ */
+int zm_moments(zm_plan_t plan, const zm_image_t* imgs, int batch, float* out,
+               unsigned flags, void* stream);
+
+/* As zm_moments, and also writes the polar samples f(rho_i, theta_k) to
+ * `fhat` (device float[batch][N_rho][N_theta]) when it is not NULL. */
+int zm_moments_ex(zm_plan_t plan, const zm_image_t* imgs, int batch, float* out,
+                  float* fhat, unsigned flags, void* stream);
+
+/* Moments of functions already sampled on the plan's polar grid:
+ * `fhat` is device float[batch][N_rho][N_theta]. */
+int zm_moments_polar(zm_plan_t plan, const float* fhat, int batch, float* out,
+                     unsigned flags, void* stream);
+
+/* Only the bilinear polar resampling (Sec. 2.5): fhat = device
+ * float[batch][N_rho][N_theta]. */
+int zm_resample(zm_plan_t plan, const zm_image_t* imgs, int batch, float* fhat,
+                void* stream);
+
+/* The two halves of zm_moments, for callers that keep the ring spectra.
+ * Spectra layout: device float[n_max+1][batch][2][N_rho] with
+ *   spectra[m][b][0][i] + j spectra[m][b][1][i] = F_m(rho_i)
+ *                       = sum_k f(rho_i, theta_k) e^{-j m theta_k}
+ * for image b (the angular transform of Eq. 1, before any weighting).
+ * zm_ring_spectra also writes the polar samples to `fhat` unless it is NULL. */
+int zm_ring_spectra(zm_plan_t plan, const zm_image_t* imgs, int batch, float* spectra,
+                    float* fhat, void* stream);
+
+/* Radial projection of given spectra (layout above, `batch` images) into
+ * moments out = device float[batch][P][2]; flags as zm_moments. */
+int zm_project(zm_plan_t plan, const float* spectra, int batch, float* out,
+               unsigned flags, void* stream);
+
+/* Number of kernels this library has launched in this process so far
+ * (a diagnostic counter; never reset). */
+unsigned long long zm_launch_count(void);
+
+/* ---- reconstruction (Eq. 9) ------------------------------------------------ */
+
+/*
+ * Reconstruction on the polar nodes:
+ *     f~(rho_i, theta_k) = Re sum_n sum_{m >= 0} c_m Z_nm R_nm(rho_i) e^{j m theta_k}
+ * with c_m = 2/eps_m (c_0 = 1, c_m = 2), the literal Eq. 9 over m = -n..n,
+ * when ZM_NEUMANN is set, and c_m = 1 (the sum over the stored m >= 0 only,
+ * which over-weights m = 0) otherwise.  `moments` is device float[batch][P][2]
+ * as written by zm_moments without ZM_NEUMANN; `out` is device
+ * float[batch][N_rho][N_theta].
+ */
+int zm_reconstruct(zm_plan_t plan, const float* moments, int batch, float* out,
+                   unsigned flags, void* stream);
+
+/*
+ * Reconstruction onto pixels: the polar reconstruction above, then bilinear
+ * interpolation in (ring, angle) at every pixel centre of each canvas inside
+ * its disk (ring bracket rho_i <= rho < rho_{i+1}, clamped to the first / last
+ * ring; angle periodic); pixels outside the disk are set to 0.  `polar_tmp`
+ * is a device float[batch][N_rho][N_theta] scratch the caller provides (it
+ * holds the polar reconstruction afterwards).
+ */
+int zm_reconstruct_cartesian(zm_plan_t plan, const float* moments, int batch,
+                             const zm_canvas_t* canvases, float* polar_tmp,
+                             unsigned flags, void* stream);
+
+/* ---- errors and normalisation (Eq. 10, Eq. 13, Table I) ------------------- */
+
+/*
+ * Per image, over the pixel centres inside the disk of `ref[b]`:
+ *   out[b][0] = eps_1 = sum (f - f~)^2 / sum f^2                  (Eq. 10)
+ *   out[b][1] = eps   = sum (f - f~)^2 / (f_max^2 * count)        (Eq. 13)
+ *   out[b][2] = f_max over the disk, out[b][3] = count
+ * `ref` and `test` are host arrays of device images of equal size; `out` is
+ * device double[batch][4].
+ */
+int zm_errors(zm_plan_t plan, const zm_image_t* ref, const zm_image_t* test,
+              int batch, double* out, void* stream);
+
+/* As zm_errors over all polar nodes (plain sums over i, k): `fhat` and
+ * `frec` are device float[batch][N_rho][N_theta]; count = N_rho N_theta. */
+int zm_errors_polar(zm_plan_t plan, const float* fhat, const float* frec,
+                    int batch, double* out, void* stream);
+
+/* min and max of each image over the pixels inside its disk: `out` is device
+ * float[batch][2] (min, max) - the per-band values Sec. 2.3 stores. */
+int zm_disk_minmax(zm_plan_t plan, const zm_image_t* imgs, int batch,
+                   float* out, void* stream);
+
+/* Min-max normalisation in place (Sec. 3, Table I): every disk pixel of
+ * canvas b is mapped linearly so that the canvas' own min / max over the disk
+ * become target[b][0] / target[b][1] (device float[batch][2]); pixels outside
+ * the disk are left unchanged. */
+int zm_minmax_normalize(zm_plan_t plan, const zm_canvas_t* canvases, int batch,
+                        const float* target, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZM_H */

@@ -1,0 +1,403 @@
+// Moments (Eq. 1): bilinear polar resampling (Sec. 2.5) fused with a real FFT of
+// every ring (the e^{-j m theta} factor), then the radial projection with the
+// (n+1)/pi weight, and the Neumann factor of Eq. 14-15.
+#include <algorithm>
+
+#include "ring_fft.cuh"
+#include "zm_internal.cuh"
+
+namespace zm {
+
+int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, cudaStream_t st);
+
+static int num_sms(int dev) {
+    static int cached[64] = {0};
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    if (dev >= 0 && dev < 64) cached[dev] = n;
+    return n;
+}
+
+// ============================================================== K-b
+constexpr int KB_MAX_IMG = 128;
+
+struct KbParams {
+    int n_rho, n_max, batch_total, b_off;
+    const float* rho32;    // [n_rho]
+    const float2* cs;      // [N] (cos theta_k, sin theta_k)
+    const float2* tw;      // [N] e^{-2 pi i j / N}
+    float* F;              // [n_max+1][batch_total][2][n_rho]
+    float* fhat_out;       // [batch_total][n_rho][N] or NULL
+    const float* fhat_in;  // [batch_total][n_rho][N] (polar input mode)
+    GeoImage img[KB_MAX_IMG];
+};
+
+enum { KB_GATHER = 0, KB_POLAR = 1, KB_RESAMPLE = 2 };
+
+// Bilinear value at pixel coordinates (X, Y); neighbours outside the image are 0.
+__device__ __forceinline__ float bilinear(const GeoImage& im, float X, float Y) {
+    const float xf = floorf(X), yf = floorf(Y);
+    const float fx = X - xf, fy = Y - yf;
+    const int x0 = (int)fminf(fmaxf(xf, -2.f), (float)im.w + 1.f);
+    const int y0 = (int)fminf(fmaxf(yf, -2.f), (float)im.h + 1.f);
+    const float* d = im.data;
+    const bool xa = (unsigned)x0 < (unsigned)im.w, xb = (unsigned)(x0 + 1) < (unsigned)im.w;
+    const bool ya = (unsigned)y0 < (unsigned)im.h, yb = (unsigned)(y0 + 1) < (unsigned)im.h;
+    const float* r0 = d + (long long)y0 * im.pitch;
+    const float* r1 = r0 + im.pitch;
+    const float p00 = (xa && ya) ? __ldg(r0 + x0) : 0.f;
+    const float p01 = (xb && ya) ? __ldg(r0 + x0 + 1) : 0.f;
+    const float p10 = (xa && yb) ? __ldg(r1 + x0) : 0.f;
+    const float p11 = (xb && yb) ? __ldg(r1 + x0 + 1) : 0.f;
+    const float top = fmaf(fx, p01 - p00, p00);
+    const float bot = fmaf(fx, p11 - p10, p10);
+    return fmaf(fy, bot - top, top);
+}
+
+// One CTA = R consecutive rings of one image, one warp per ring (R = blockDim/32).
+// Phase 1: the R x N samples into shared memory (bilinear gather, or a copy of
+// given polar samples).  Phase 2: per warp, the N-point real FFT of its ring
+// as an N/2-point complex FFT plus the split
+//   F_m = (Z_m + conj Z_{M-m})/2 + e^{-2 pi i m/N} (Z_m - conj Z_{M-m})/(2i),
+// for m = 0..n_max.  Phase 3: F[m][b][re/im][i0..i0+R) written as segments.
+template <int LOGN, int MODE>
+__global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ KbParams p) {
+    using FFT = RingFFT<LOGN>;
+    constexpr int N = FFT::N;
+    constexpr int ROW = FFT::ROW_FLOATS;
+    extern __shared__ __align__(16) float smem[];
+    const int R = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bl = blockIdx.y;
+    const int b = p.b_off + bl;
+    const int i0 = blockIdx.x * R;
+    const int n_rho = p.n_rho;
+    float* rings = smem;
+
+    if (MODE == KB_POLAR) {
+        for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+            const int r = idx >> LOGN, k = idx & (N - 1);
+            const int i = i0 + r;
+            rings[r * ROW + k] = (i < n_rho) ? __ldg(&p.fhat_in[((size_t)b * n_rho + i) * N + k]) : 0.f;
+        }
+    } else {
+        const GeoImage im = p.img[bl];
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+            const int r = idx >> LOGN, k = idx & (N - 1);
+            const int i = i0 + r;
+            float v = 0.f;
+            if (i < n_rho) {
+                const float rad = im.r * __ldg(&p.rho32[i]);
+                const float2 c = __ldg(&p.cs[k]);
+                v = bilinear(im, fmaf(rad, c.x, im.cx), fmaf(-rad, c.y, im.cy));
+                if (p.fhat_out) p.fhat_out[((size_t)b * n_rho + i) * N + k] = v;
+            }
+            rings[r * ROW + k] = v;
+        }
+    }
+    if (MODE == KB_RESAMPLE) return;
+    __syncthreads();
+
+    const int n_max = p.n_max;
+    float* Fs = smem + R * ROW;                  // [2][n_max+1][R]
+    {
+        float* row = rings + warp * ROW;
+        float2 v[FFT::Q];
+        const float2* z = reinterpret_cast<const float2*>(row);
+#pragma unroll
+        for (int s = 0; s < FFT::Q; ++s)
+            v[s] = (lane < FFT::L) ? z[lane + FFT::L * s] : make_float2(0.f, 0.f);
+        __syncwarp();
+        FFT::forward(v, lane, p.tw);
+        float2* X = reinterpret_cast<float2*>(row);
+        if (lane < FFT::L) {
+#pragma unroll
+            for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::out_index(r, lane))] = v[r];
+        }
+        __syncwarp();
+        for (int m = lane; m <= n_max; m += 32) {
+            const float2 A = X[FFT::pad(m)];
+            const float2 B = cconj(X[FFT::pad((FFT::M - m) & (FFT::M - 1))]);
+            const float2 E = cscale(cadd(A, B), 0.5f);
+            const float2 D = csub(A, B);
+            const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+            const float2 Fm = cadd(E, cmul(__ldg(&p.tw[m]), O));
+            Fs[m * R + warp] = Fm.x;
+            Fs[((n_max + 1) + m) * R + warp] = Fm.y;
+        }
+    }
+    __syncthreads();
+    const int tot = 2 * (n_max + 1) * R;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int r = e % R;
+        const int cm = e / R;
+        const int c = cm / (n_max + 1);
+        const int m = cm - c * (n_max + 1);
+        const int i = i0 + r;
+        if (i < n_rho) p.F[(((size_t)m * p.batch_total + b) * 2 + c) * n_rho + i] = Fs[e];
+    }
+}
+
+template <int LOGN, int MODE>
+static int launch_kb_t(const KbParams& kp, int R, int nb, cudaStream_t st) {
+    using FFT = RingFFT<LOGN>;
+    const size_t smem = sizeof(float) * ((size_t)R * FFT::ROW_FLOATS +
+                                         (MODE == KB_RESAMPLE ? 0 : (size_t)2 * (kp.n_max + 1) * R));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static size_t configured[64] = {0};
+    if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_ring_spectra<LOGN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        if (dev < 64) configured[dev] = smem;
+    }
+    dim3 grid((kp.n_rho + R - 1) / R, nb);
+    k_ring_spectra<LOGN, MODE><<<grid, R * 32, smem, st>>>(kp);
+    ZM_LAUNCH_CHECK("k_ring_spectra");
+    return ZM_OK;
+}
+
+template <int MODE>
+static int launch_kb_mode(int logn, const KbParams& kp, int R, int nb, cudaStream_t st) {
+    switch (logn) {
+        case 3: return launch_kb_t<3, MODE>(kp, R, nb, st);
+        case 4: return launch_kb_t<4, MODE>(kp, R, nb, st);
+        case 5: return launch_kb_t<5, MODE>(kp, R, nb, st);
+        case 6: return launch_kb_t<6, MODE>(kp, R, nb, st);
+        case 7: return launch_kb_t<7, MODE>(kp, R, nb, st);
+        case 8: return launch_kb_t<8, MODE>(kp, R, nb, st);
+        case 9: return launch_kb_t<9, MODE>(kp, R, nb, st);
+        case 10: return launch_kb_t<10, MODE>(kp, R, nb, st);
+        case 11: return launch_kb_t<11, MODE>(kp, R, nb, st);
+        default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", logn);
+    }
+}
+
+// ============================================================== K-c (FP32)
+// For each m: the (K_m x N_rho) x (N_rho x 2B) product
+//   D[n][col] = sum_i A[row(m,n)][i] F[m][col][i],   col = 2b + re/im,
+// split over i into S partial sums (part[s][row][col]); k_project_reduce adds
+// them in a fixed order and applies the Neumann factor.
+constexpr int KC_ROWS = 64, KC_COLS = 32, KC_K = 32;
+
+__global__ void __launch_bounds__(256)
+k_project_fp32(const float* __restrict__ A32, const float* __restrict__ F, const int* __restrict__ mrow,
+               int n_max, int n_rho, int ncol, int chunk, int P, float* __restrict__ part) {
+    __shared__ float As[KC_K][KC_ROWS + 1];
+    __shared__ float Fs[KC_K][KC_COLS + 1];
+    const int m = blockIdx.x;
+    const int col0 = blockIdx.y * KC_COLS;
+    const int s = blockIdx.z;
+    const int Km = (n_max - m) / 2 + 1;
+    const int rowbase = mrow[m];
+    const int ib = s * chunk, ie = min(n_rho, ib + chunk);
+    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+    const float* Fm = F + ((size_t)m * ncol + col0) * n_rho;
+    for (int rt = 0; rt < Km; rt += KC_ROWS) {
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int kk = ib; kk < ie; kk += KC_K) {
+            for (int e = tid; e < KC_ROWS * KC_K; e += 256) {
+                const int row = e >> 5, k = e & 31;
+                const int gr = rt + row, gk = kk + k;
+                As[k][row] = (gr < Km && gk < ie) ? __ldg(&A32[(size_t)(rowbase + gr) * n_rho + gk]) : 0.f;
+            }
+            for (int e = tid; e < KC_COLS * KC_K; e += 256) {
+                const int col = e >> 5, k = e & 31;
+                const int gk = kk + k;
+                Fs[k][col] = (col0 + col < ncol && gk < ie) ? __ldg(&Fm[(size_t)col * n_rho + gk]) : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int k = 0; k < KC_K; ++k) {
+                const float a0 = As[k][2 * ty], a1 = As[k][2 * ty + 1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float f = Fs[k][4 * tx + j];
+                    acc[0][j] = fmaf(a0, f, acc[0][j]);
+                    acc[1][j] = fmaf(a1, f, acc[1][j]);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int gr = rt + 2 * ty + a;
+            if (gr >= Km) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int col = col0 + 4 * tx + j;
+                if (col < ncol) part[((size_t)s * P + rowbase + gr) * ncol + col] = acc[a][j];
+            }
+        }
+    }
+}
+
+__global__ void k_project_reduce(const float* __restrict__ part, int S, int P, int ncol,
+                                 const int2* __restrict__ pair_nm, const int* __restrict__ mrow,
+                                 int batch, int neumann, float* __restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= batch * P) return;
+    const int b = idx / P, q = idx - b * P;
+    const int2 nm = pair_nm[q];
+    const int row = mrow[nm.y] + (nm.x - nm.y) / 2;
+    float re = 0.f, im = 0.f;
+    for (int s = 0; s < S; ++s) {
+        const float* ps = part + ((size_t)s * P + row) * ncol + 2 * b;
+        re += ps[0];
+        im += ps[1];
+    }
+    const float f = (neumann && nm.y == 0) ? 0.5f : 1.f;
+    out[(size_t)idx * 2] = re * f;
+    out[(size_t)idx * 2 + 1] = im * f;
+}
+
+static int launch_projection_fp32(zm_plan_t p, const float* F, int batch, float* out, unsigned flags,
+                                  cudaStream_t st) {
+    const int ncol = 2 * batch;
+    const int ctiles = (ncol + KC_COLS - 1) / KC_COLS;
+    const int base = (p->n_max + 1) * ctiles;
+    const int target = 4 * num_sms(p->device);
+    const int kchunks = (p->n_rho + KC_K - 1) / KC_K;
+    int S = std::max(1, std::min(kchunks, (target + base - 1) / base));
+    const int chunk = ((kchunks + S - 1) / S) * KC_K;
+    S = (p->n_rho + chunk - 1) / chunk;
+    int st_ = p->ws_part.grow(sizeof(float) * (size_t)S * p->P * ncol);
+    if (st_ != ZM_OK) return st_;
+    float* part = (float*)p->ws_part.ptr;
+    dim3 grid(p->n_max + 1, ctiles, S);
+    k_project_fp32<<<grid, 256, 0, st>>>(p->A32, F, p->mrow, p->n_max, p->n_rho, ncol,
+                                          chunk, p->P, part);
+    ZM_LAUNCH_CHECK("k_project_fp32");
+    const int tot = batch * p->P;
+    k_project_reduce<<<(tot + 255) / 256, 256, 0, st>>>(part, S, p->P, ncol, p->pair_nm, p->mrow, batch,
+                                                         (flags & ZM_NEUMANN) ? 1 : 0, out);
+    ZM_LAUNCH_CHECK("k_project_reduce");
+    return ZM_OK;
+}
+
+// ============================================================== driver
+static int pick_rings(zm_plan_t p, int batch) {
+    int R = 8;
+    const int want = 2 * num_sms(p->device);
+    while (R > 2 && ((p->n_rho + R - 1) / R) * batch < want) R >>= 1;
+    return R;
+}
+
+int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* F,
+                   float* fhat_out, bool resample_only, cudaStream_t st) {
+    const int R = pick_rings(p, batch);
+    p->kb_rings = R;
+    const int mode = fhat_in ? KB_POLAR : (resample_only ? KB_RESAMPLE : KB_GATHER);
+    static thread_local KbParams kp;
+    kp.n_rho = p->n_rho;
+    kp.n_max = p->n_max;
+    kp.batch_total = batch;
+    kp.rho32 = p->rho32;
+    kp.cs = p->cs;
+    kp.tw = p->tw;
+    kp.F = F;
+    kp.fhat_out = fhat_out;
+    kp.fhat_in = fhat_in;
+    for (int b0 = 0; b0 < batch; b0 += KB_MAX_IMG) {
+        const int nb = std::min(KB_MAX_IMG, batch - b0);
+        kp.b_off = b0;
+        if (imgs)
+            for (int j = 0; j < nb; ++j) kp.img[j] = resolve(imgs[b0 + j]);
+        int s;
+        if (mode == KB_POLAR) s = launch_kb_mode<KB_POLAR>(p->log_theta, kp, R, nb, st);
+        else if (mode == KB_RESAMPLE) s = launch_kb_mode<KB_RESAMPLE>(p->log_theta, kp, R, nb, st);
+        else s = launch_kb_mode<KB_GATHER>(p->log_theta, kp, R, nb, st);
+        if (s != ZM_OK) return s;
+    }
+    return ZM_OK;
+}
+
+int launch_projection(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, cudaStream_t st) {
+    if (p->prec == PREC_FP32) return launch_projection_fp32(p, F, batch, out, flags, st);
+    return launch_projection_tc(p, F, batch, out, flags, st);
+}
+
+}  // namespace zm
+
+using namespace zm;
+
+static int moments_common(zm_plan_t plan, const zm_image_t* imgs, const float* fhat_in, int batch, float* out,
+                          float* fhat_out, unsigned flags, void* stream) {
+    if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1 (got %d)", batch);
+    if (!out) return set_error(ZM_EINVAL, "output pointer is NULL");
+    if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
+    if (!fhat_in) {
+        const int s = check_images(imgs, batch);
+        if (s != ZM_OK) return s;
+    }
+    DeviceGuard g(plan->device);
+    if (!g.ok) return set_error(ZM_ECUDA, "cannot select device %d", plan->device);
+    int s = plan->ws_F.grow(sizeof(float) * (size_t)(plan->n_max + 1) * batch * 2 * plan->n_rho);
+    if (s != ZM_OK) return s;
+    float* F = (float*)plan->ws_F.ptr;
+    s = launch_spectra(plan, imgs, fhat_in, batch, F, fhat_out, false, (cudaStream_t)stream);
+    if (s != ZM_OK) return s;
+    return launch_projection(plan, F, batch, out, flags, (cudaStream_t)stream);
+}
+
+extern "C" int zm_moments(zm_plan_t plan, const zm_image_t* imgs, int batch, float* out, unsigned flags,
+                          void* stream) {
+    return moments_common(plan, imgs, nullptr, batch, out, nullptr, flags, stream);
+}
+
+extern "C" int zm_moments_ex(zm_plan_t plan, const zm_image_t* imgs, int batch, float* out, float* fhat,
+                             unsigned flags, void* stream) {
+    return moments_common(plan, imgs, nullptr, batch, out, fhat, flags, stream);
+}
+
+extern "C" int zm_moments_polar(zm_plan_t plan, const float* fhat, int batch, float* out, unsigned flags,
+                                void* stream) {
+    if (!fhat) return set_error(ZM_EINVAL, "fhat is NULL");
+    return moments_common(plan, nullptr, fhat, batch, out, nullptr, flags, stream);
+}
+
+extern "C" int zm_resample(zm_plan_t plan, const zm_image_t* imgs, int batch, float* fhat, void* stream) {
+    if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
+    if (!fhat) return set_error(ZM_EINVAL, "fhat is NULL");
+    const int s = check_images(imgs, batch);
+    if (s != ZM_OK) return s;
+    DeviceGuard g(plan->device);
+    return launch_spectra(plan, imgs, nullptr, batch, nullptr, fhat, true, (cudaStream_t)stream);
+}
+
+extern "C" int zm_ring_spectra(zm_plan_t plan, const zm_image_t* imgs, int batch, float* spectra, float* fhat,
+                               void* stream) {
+    if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
+    if (!spectra) return set_error(ZM_EINVAL, "spectra is NULL");
+    const int s = check_images(imgs, batch);
+    if (s != ZM_OK) return s;
+    DeviceGuard g(plan->device);
+    return launch_spectra(plan, imgs, nullptr, batch, spectra, fhat, false, (cudaStream_t)stream);
+}
+
+extern "C" int zm_project(zm_plan_t plan, const float* spectra, int batch, float* out, unsigned flags,
+                          void* stream) {
+    if (!plan || !spectra || !out) return set_error(ZM_EINVAL, "NULL argument");
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1 (got %d)", batch);
+    if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
+    DeviceGuard g(plan->device);
+    return launch_projection(plan, spectra, batch, out, flags, (cudaStream_t)stream);
+}
+
+extern "C" int zm_plan_reserve(zm_plan_t plan, int batch) {
+    if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
+    DeviceGuard g(plan->device);
+    int s = plan->ws_F.grow(sizeof(float) * (size_t)(plan->n_max + 1) * batch * 2 * plan->n_rho);
+    if (s != ZM_OK) return s;
+    // generous bound for the projection partials (S <= N_rho / 32 + 1)
+    const int S = std::min((plan->n_rho + KC_K - 1) / KC_K, 4 * num_sms(plan->device));
+    s = plan->ws_part.grow(sizeof(float) * (size_t)S * plan->P * 2 * batch);
+    if (s != ZM_OK) return s;
+    s = plan->ws_G.grow(sizeof(float) * (size_t)(plan->n_max + 1) * batch * 2 * plan->n_rho);
+    if (s != ZM_OK) return s;
+    return ZM_OK;
+}

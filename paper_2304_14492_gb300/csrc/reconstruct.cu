@@ -1,0 +1,521 @@
+// Reconstruction (Eq. 9) as the transpose of the moment path: a radial
+// contraction G_m(rho_i) = c_m sum_n Z_nm R_nm(rho_i), an inverse real FFT per
+// ring, and optional interpolation onto pixels; the reconstruction errors of
+// Eq. 10 and Eq. 13 and the min-max normalisation of Sec. 3 / Table I.
+#include <algorithm>
+
+#include "ring_fft.cuh"
+#include "zm_internal.cuh"
+
+namespace zm {
+
+constexpr int KD_MAX_IMG = 128;
+constexpr float kTwoPi = 6.28318530717958647692f;
+
+// ============================================================== radial part
+// G[b][m][re/im][i] = c_m sum_{n = m, m+2, ..} R_nm(rho_i) Z_nm, with
+// c_m = 2/eps_m (c_0 = 1, c_m = 2) for the literal Eq. 9 and c_m = 1 for the
+// half sum over the stored m >= 0.
+__global__ void __launch_bounds__(128)
+k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, const int* __restrict__ mrow,
+               int n_max, int n_rho, int P, int neumann, float* __restrict__ G) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y;
+    const int b = blockIdx.z;
+    if (i >= n_rho) return;
+    const int Km = (n_max - m) / 2 + 1;
+    const int row0 = mrow[m];
+    const float2* Zb = Z + (size_t)b * P;
+    float re = 0.f, im = 0.f;
+    for (int j = 0; j < Km; ++j) {
+        const float r = __ldg(&R32m[(size_t)(row0 + j) * n_rho + i]);
+        const float2 z = __ldg(&Zb[moment_index(m + 2 * j, m)]);
+        re = fmaf(r, z.x, re);
+        im = fmaf(r, z.y, im);
+    }
+    const float c = (neumann && m > 0) ? 2.f : 1.f;
+    float* g = G + (((size_t)b * (n_max + 1) + m) * 2) * n_rho + i;
+    g[0] = c * re;
+    g[n_rho] = c * im;
+}
+
+// ============================================================== ring inverse FFT
+// f~_k = Re sum_{m=0}^{n_max} G_m e^{2 pi i m k / N}.  With the Hermitian
+// spectrum S (S_0 = 2 Re G_0, S_m = G_m, S_{N-m} = conj G_m) and
+// x_k = sum_m S_m e^{2 pi i m k/N} = 2 f~_k, the packed z_j = x_{2j} + i x_{2j+1}
+// is the M-point inverse DFT of
+//   C_m = (S_m + conj S_{M-m}) + i e^{2 pi i m/N} (S_m - conj S_{M-m}),
+// computed as conj(DFT(conj C)) by the same warp FFT as the forward path.
+template <int LOGN>
+__global__ void __launch_bounds__(512)
+k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho,
+             float* __restrict__ out) {
+    using FFT = RingFFT<LOGN>;
+    constexpr int N = FFT::N;
+    constexpr int M = FFT::M;
+    constexpr int ROW = FFT::ROW_FLOATS;
+    extern __shared__ __align__(16) float smem[];
+    const int R = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.y;
+    const int i0 = blockIdx.x * R;
+    float* rows = smem;                                         // [R][ROW]
+    float2* Gs = reinterpret_cast<float2*>(smem + R * ROW);     // [R][n_max+1]
+    const int nm1 = n_max + 1;
+    for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
+        const int r = e % R, m = e / R;
+        const int i = i0 + r;
+        float2 g = make_float2(0.f, 0.f);
+        if (i < n_rho) {
+            const float* gp = G + (((size_t)b * nm1 + m) * 2) * n_rho + i;
+            g = make_float2(__ldg(gp), __ldg(gp + n_rho));
+        }
+        Gs[r * nm1 + m] = g;
+    }
+    __syncthreads();
+    const float2* Gr = Gs + warp * nm1;
+    float2 v[FFT::Q];
+#pragma unroll
+    for (int s = 0; s < FFT::Q; ++s) {
+        const int m = (lane & (FFT::L - 1)) + FFT::L * s;
+        float2 Sm = make_float2(0.f, 0.f), T = make_float2(0.f, 0.f);
+        if (m <= n_max) Sm = (m == 0) ? make_float2(2.f * Gr[0].x, 0.f) : Gr[m];
+        const int q = M - m;
+        if (q >= 1 && q <= n_max) T = cconj(Gr[q]);
+        const float2 w = __ldg(&tw[m]);                  // e^{-2 pi i m/N}
+        const float2 ie = make_float2(w.y, w.x);         // i e^{+2 pi i m/N} = i conj(w)
+        const float2 C = cadd(cadd(Sm, T), cmul(ie, csub(Sm, T)));
+        v[s] = (lane < FFT::L) ? cconj(C) : make_float2(0.f, 0.f);
+    }
+    FFT::forward(v, lane, tw);
+    float2* X = reinterpret_cast<float2*>(rows + warp * ROW);
+    if (lane < FFT::L) {
+#pragma unroll
+        for (int r = 0; r < FFT::Q; ++r)
+            X[FFT::pad(FFT::out_index(r, lane))] = make_float2(0.5f * v[r].x, -0.5f * v[r].y);
+    }
+    __syncwarp();
+    const int i = i0 + warp;
+    if (i < n_rho) {
+        float2* o = reinterpret_cast<float2*>(out + ((size_t)b * n_rho + i) * N);
+        for (int j = lane; j < M; j += 32) o[j] = X[FFT::pad(j)];
+    }
+}
+
+template <int LOGN>
+static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho, int batch, float* out,
+                         cudaStream_t st) {
+    using FFT = RingFFT<LOGN>;
+    const int R = 8;
+    const size_t smem = sizeof(float) * (size_t)R * FFT::ROW_FLOATS + sizeof(float2) * (size_t)R * (n_max + 1);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static size_t configured[64] = {0};
+    if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_recon_ifft<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev < 64) configured[dev] = smem;
+    }
+    dim3 grid((n_rho + R - 1) / R, batch);
+    k_recon_ifft<LOGN><<<grid, R * 32, smem, st>>>(G, tw, n_max, n_rho, out);
+    ZM_LAUNCH_CHECK("k_recon_ifft");
+    return ZM_OK;
+}
+
+int launch_reconstruct(zm_plan_t p, const float* moments, int batch, float* out, unsigned flags,
+                       cudaStream_t st) {
+    const int s = p->ws_G.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
+    if (s != ZM_OK) return s;
+    float* G = (float*)p->ws_G.ptr;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nb = std::min(65535, batch - b0);
+        dim3 grid((p->n_rho + 127) / 128, p->n_max + 1, nb);
+        k_recon_radial<<<grid, 128, 0, st>>>(p->R32m, (const float2*)moments + (size_t)b0 * p->P, p->mrow, p->n_max,
+                                              p->n_rho, p->P, (flags & ZM_NEUMANN) ? 1 : 0,
+                                              G + (size_t)b0 * (p->n_max + 1) * 2 * p->n_rho);
+        ZM_LAUNCH_CHECK("k_recon_radial");
+    }
+    switch (p->log_theta) {
+        case 3: return launch_ifft_t<3>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 4: return launch_ifft_t<4>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 5: return launch_ifft_t<5>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 6: return launch_ifft_t<6>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 7: return launch_ifft_t<7>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 8: return launch_ifft_t<8>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 9: return launch_ifft_t<9>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 10: return launch_ifft_t<10>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        case 11: return launch_ifft_t<11>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
+        default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", p->log_theta);
+    }
+}
+
+// ============================================================== pixels
+struct CanvasDesc {
+    float* data;
+    long long pitch;
+    int h, w;
+    float cx, cy, r;
+};
+
+// Pixel centre (x, y) -> (rho, theta) in the disk's frame; same float
+// arithmetic everywhere a disk membership is decided.
+__device__ __forceinline__ float pixel_rho(float x, float y, float cx, float cy, float r, float* dx, float* dy) {
+    *dx = x - cx;
+    *dy = cy - y;
+    return sqrtf((*dx) * (*dx) + (*dy) * (*dy)) / r;
+}
+
+struct CartParams {
+    int n_rho, n_theta, b_off;
+    const float* rho32;
+    const float* polar;     // [batch][n_rho][n_theta]
+    CanvasDesc cv[KD_MAX_IMG];
+};
+
+__global__ void __launch_bounds__(256) k_polar_to_cart(const __grid_constant__ CartParams p) {
+    const CanvasDesc c = p.cv[blockIdx.z];
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= c.w || y >= c.h) return;
+    float dx, dy;
+    const float rho = pixel_rho((float)x, (float)y, c.cx, c.cy, c.r, &dx, &dy);
+    float val = 0.f;
+    if (rho <= 1.f) {
+        float th = atan2f(dy, dx);
+        if (th < 0.f) th += kTwoPi;
+        const int n_rho = p.n_rho, N = p.n_theta;
+        int lo = 0, hi = n_rho;                 // first node > rho
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&p.rho32[mid]) > rho) hi = mid; else lo = mid + 1;
+        }
+        const int i1 = min(lo, n_rho - 1);
+        const int i0 = max(min(lo - 1, n_rho - 1), 0);
+        const float r0 = __ldg(&p.rho32[i0]), r1 = __ldg(&p.rho32[i1]);
+        const float span = r1 - r0;
+        float t = span > 0.f ? (rho - r0) / span : 0.f;
+        t = fminf(fmaxf(t, 0.f), 1.f);
+        const float v = th * (float)N / kTwoPi;
+        const float kf = floorf(v);
+        const float s = v - kf;
+        const int k0 = ((int)kf) & (N - 1);
+        const int k1 = (k0 + 1) & (N - 1);
+        const float* pb = p.polar + (size_t)(p.b_off + blockIdx.z) * n_rho * N;
+        const float a0 = __ldg(&pb[(size_t)i0 * N + k0]), a1 = __ldg(&pb[(size_t)i0 * N + k1]);
+        const float b0 = __ldg(&pb[(size_t)i1 * N + k0]), b1 = __ldg(&pb[(size_t)i1 * N + k1]);
+        const float ra = fmaf(s, a1 - a0, a0), rb = fmaf(s, b1 - b0, b0);
+        val = fmaf(t, rb - ra, ra);
+    }
+    c.data[(size_t)y * c.pitch + x] = val;
+}
+
+static CanvasDesc resolve_canvas(const zm_canvas_t& cv) {
+    zm_image_t im{cv.data, cv.height, cv.width, cv.pitch, cv.cx, cv.cy, cv.radius};
+    const GeoImage g = resolve(im);
+    return CanvasDesc{cv.data, g.pitch, g.h, g.w, g.cx, g.cy, g.r};
+}
+
+int launch_polar_to_cart(zm_plan_t p, const float* polar, int batch, const zm_canvas_t* cv, cudaStream_t st) {
+    static thread_local CartParams cp;
+    cp.n_rho = p->n_rho;
+    cp.n_theta = p->n_theta;
+    cp.rho32 = p->rho32;
+    cp.polar = polar;
+    for (int b0 = 0; b0 < batch; b0 += KD_MAX_IMG) {
+        const int nb = std::min(KD_MAX_IMG, batch - b0);
+        cp.b_off = b0;
+        int hmax = 1, wmax = 1;
+        for (int j = 0; j < nb; ++j) {
+            cp.cv[j] = resolve_canvas(cv[b0 + j]);
+            hmax = std::max(hmax, cp.cv[j].h);
+            wmax = std::max(wmax, cp.cv[j].w);
+        }
+        dim3 grid((wmax + 31) / 32, (hmax + 7) / 8, nb);
+        k_polar_to_cart<<<grid, dim3(32, 8), 0, st>>>(cp);
+        ZM_LAUNCH_CHECK("k_polar_to_cart");
+    }
+    return ZM_OK;
+}
+
+// ============================================================== reductions
+constexpr int RED_BLOCKS = 64;
+constexpr int RED_THREADS = 256;
+
+struct RedParams {
+    int mode;                 // 0: errors over disk pixels, 1: errors over polar nodes, 2: min/max over disk
+    int n_nodes, b_off;
+    const float* fhat;        // mode 1
+    const float* frec;        // mode 1
+    double* part;             // [batch][RED_BLOCKS][4]
+    CanvasDesc ref[KD_MAX_IMG];
+    CanvasDesc tst[KD_MAX_IMG];
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per block: (sum (f - g)^2, sum f^2, max f, count) for the error modes and
+// (min, max, -, count) for the min/max mode; float partials per thread, one
+// double record per block.
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const __grid_constant__ RedParams p) {
+    const int bl = blockIdx.y;
+    const int b = p.b_off + bl;
+    float s0 = 0.f, s1 = 0.f, mx = -INFINITY, mn = INFINITY;
+    float cnt = 0.f;
+    if (p.mode == 1) {
+        const float* f = p.fhat + (size_t)b * p.n_nodes;
+        const float* g = p.frec + (size_t)b * p.n_nodes;
+        for (int e = blockIdx.x * RED_THREADS + threadIdx.x; e < p.n_nodes; e += RED_BLOCKS * RED_THREADS) {
+            const float fv = __ldg(&f[e]);
+            const float d = fv - __ldg(&g[e]);
+            s0 = fmaf(d, d, s0);
+            s1 = fmaf(fv, fv, s1);
+            mx = fmaxf(mx, fv);
+            cnt += 1.f;
+        }
+    } else {
+        const CanvasDesc c = p.ref[bl];
+        const CanvasDesc t = p.tst[bl];
+        for (int y = blockIdx.x; y < c.h; y += RED_BLOCKS) {
+            for (int x = threadIdx.x; x < c.w; x += RED_THREADS) {
+                float dx, dy;
+                if (pixel_rho((float)x, (float)y, c.cx, c.cy, c.r, &dx, &dy) > 1.f) continue;
+                const float fv = __ldg(&c.data[(size_t)y * c.pitch + x]);
+                if (p.mode == 0) {
+                    const float d = fv - __ldg(&t.data[(size_t)y * t.pitch + x]);
+                    s0 = fmaf(d, d, s0);
+                    s1 = fmaf(fv, fv, s1);
+                }
+                mx = fmaxf(mx, fv);
+                mn = fminf(mn, fv);
+                cnt += 1.f;
+            }
+        }
+    }
+    __shared__ float sh[4][RED_THREADS / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    mx = warp_max(mx);
+    mn = warp_min(mn);
+    cnt = warp_sum(cnt);
+    if (l == 0) {
+        sh[0][w] = s0;
+        sh[1][w] = p.mode == 2 ? mn : s1;
+        sh[2][w] = mx;
+        sh[3][w] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, c1 = 0, c3 = 0;
+        float m2 = -INFINITY, m1 = INFINITY;
+        for (int j = 0; j < RED_THREADS / 32; ++j) {
+            a += sh[0][j];
+            if (p.mode == 2) m1 = fminf(m1, sh[1][j]); else c1 += sh[1][j];
+            m2 = fmaxf(m2, sh[2][j]);
+            c3 += sh[3][j];
+        }
+        double* o = p.part + ((size_t)b * RED_BLOCKS + blockIdx.x) * 4;
+        o[0] = a;
+        o[1] = p.mode == 2 ? (double)m1 : c1;
+        o[2] = (double)m2;
+        o[3] = c3;
+    }
+}
+
+// mode 0/1: out[b] = (eps_1, eps, f_max, count) as doubles; mode 2: mm[b] = (min, max)
+__global__ void k_reduce_final(const double* __restrict__ part, int batch, int mode, double* __restrict__ out,
+                               float* __restrict__ mm) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    double sd = 0, sf = 0, cnt = 0, mx = -INFINITY, mn = INFINITY;
+    for (int j = 0; j < RED_BLOCKS; ++j) {
+        const double* o = part + ((size_t)b * RED_BLOCKS + j) * 4;
+        sd += o[0];
+        if (mode == 2) mn = fmin(mn, o[1]); else sf += o[1];
+        mx = fmax(mx, o[2]);
+        cnt += o[3];
+    }
+    if (mode == 2) {
+        mm[2 * b] = (float)mn;
+        mm[2 * b + 1] = (float)mx;
+    } else {
+        out[4 * b + 0] = sd / sf;
+        out[4 * b + 1] = sd / (mx * mx * cnt);
+        out[4 * b + 2] = mx;
+        out[4 * b + 3] = cnt;
+    }
+}
+
+static int run_reduce(zm_plan_t p, int mode, const zm_image_t* ref, const zm_image_t* tst, const float* fhat,
+                      const float* frec, int batch, double* out, float* mm, cudaStream_t st) {
+    int s = p->ws_red.grow(sizeof(double) * (size_t)batch * RED_BLOCKS * 4);
+    if (s != ZM_OK) return s;
+    static thread_local RedParams rp;
+    rp.mode = mode;
+    rp.n_nodes = p->n_rho * p->n_theta;
+    rp.fhat = fhat;
+    rp.frec = frec;
+    rp.part = (double*)p->ws_red.ptr;
+    for (int b0 = 0; b0 < batch; b0 += KD_MAX_IMG) {
+        const int nb = std::min(KD_MAX_IMG, batch - b0);
+        rp.b_off = b0;
+        if (mode != 1) {
+            for (int j = 0; j < nb; ++j) {
+                const GeoImage g = resolve(ref[b0 + j]);
+                rp.ref[j] = CanvasDesc{const_cast<float*>(g.data), g.pitch, g.h, g.w, g.cx, g.cy, g.r};
+                if (mode == 0) {
+                    const GeoImage t = resolve(tst[b0 + j]);
+                    rp.tst[j] = CanvasDesc{const_cast<float*>(t.data), t.pitch, t.h, t.w, t.cx, t.cy, t.r};
+                }
+            }
+        }
+        k_reduce<<<dim3(RED_BLOCKS, nb), RED_THREADS, 0, st>>>(rp);
+        ZM_LAUNCH_CHECK("k_reduce");
+    }
+    k_reduce_final<<<(batch + 127) / 128, 128, 0, st>>>((const double*)p->ws_red.ptr, batch, mode, out, mm);
+    ZM_LAUNCH_CHECK("k_reduce_final");
+    return ZM_OK;
+}
+
+int launch_errors(zm_plan_t p, const zm_image_t* ref, const zm_image_t* test, const float* fhat,
+                  const float* frec, int batch, double* out, cudaStream_t st) {
+    return run_reduce(p, fhat ? 1 : 0, ref, test, fhat, frec, batch, out, nullptr, st);
+}
+
+int launch_disk_minmax(zm_plan_t p, const zm_image_t* imgs, int batch, float* out, cudaStream_t st) {
+    return run_reduce(p, 2, imgs, nullptr, nullptr, nullptr, batch, nullptr, out, st);
+}
+
+struct NormParams {
+    const float* mm;          // [batch][2] canvas min / max
+    const float* target;      // [batch][2] wanted min / max
+    int b_off;
+    CanvasDesc cv[KD_MAX_IMG];
+};
+
+__global__ void __launch_bounds__(256) k_minmax_apply(const __grid_constant__ NormParams p) {
+    const CanvasDesc c = p.cv[blockIdx.z];
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= c.w || y >= c.h) return;
+    float dx, dy;
+    if (pixel_rho((float)x, (float)y, c.cx, c.cy, c.r, &dx, &dy) > 1.f) return;
+    const int b = p.b_off + blockIdx.z;
+    const float gmin = p.mm[2 * b], gmax = p.mm[2 * b + 1];
+    const float lo = p.target[2 * b], hi = p.target[2 * b + 1];
+    const float scale = gmax > gmin ? (hi - lo) / (gmax - gmin) : 0.f;
+    float* px = c.data + (size_t)y * c.pitch + x;
+    *px = fmaf(*px - gmin, scale, lo);
+}
+
+int launch_minmax_normalize(zm_plan_t p, const zm_canvas_t* cv, int batch, const float* target, cudaStream_t st) {
+    int s = p->ws_scale.grow(sizeof(float) * 2 * (size_t)batch);
+    if (s != ZM_OK) return s;
+    std::vector<zm_image_t> ims(batch);
+    for (int b = 0; b < batch; ++b)
+        ims[b] = zm_image_t{cv[b].data, cv[b].height, cv[b].width, cv[b].pitch, cv[b].cx, cv[b].cy, cv[b].radius};
+    float* mm = (float*)p->ws_scale.ptr;
+    s = run_reduce(p, 2, ims.data(), nullptr, nullptr, nullptr, batch, nullptr, mm, st);
+    if (s != ZM_OK) return s;
+    static thread_local NormParams np;
+    np.mm = mm;
+    np.target = target;
+    for (int b0 = 0; b0 < batch; b0 += KD_MAX_IMG) {
+        const int nb = std::min(KD_MAX_IMG, batch - b0);
+        np.b_off = b0;
+        int hmax = 1, wmax = 1;
+        for (int j = 0; j < nb; ++j) {
+            np.cv[j] = resolve_canvas(cv[b0 + j]);
+            hmax = std::max(hmax, np.cv[j].h);
+            wmax = std::max(wmax, np.cv[j].w);
+        }
+        k_minmax_apply<<<dim3((wmax + 31) / 32, (hmax + 7) / 8, nb), dim3(32, 8), 0, st>>>(np);
+        ZM_LAUNCH_CHECK("k_minmax_apply");
+    }
+    return ZM_OK;
+}
+
+}  // namespace zm
+
+using namespace zm;
+
+static int check_canvases(const zm_canvas_t* cv, int batch) {
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
+    if (!cv) return set_error(ZM_EINVAL, "canvas array is NULL");
+    for (int b = 0; b < batch; ++b) {
+        if (!cv[b].data) return set_error(ZM_EINVAL, "canvas %d: data is NULL", b);
+        if (cv[b].height < 1 || cv[b].width < 1 || cv[b].pitch < cv[b].width)
+            return set_error(ZM_EINVAL, "canvas %d: bad size / pitch", b);
+    }
+    return ZM_OK;
+}
+
+extern "C" int zm_reconstruct(zm_plan_t plan, const float* moments, int batch, float* out, unsigned flags,
+                              void* stream) {
+    if (!plan || !moments || !out) return set_error(ZM_EINVAL, "NULL argument");
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
+    if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
+    DeviceGuard g(plan->device);
+    return launch_reconstruct(plan, moments, batch, out, flags, (cudaStream_t)stream);
+}
+
+extern "C" int zm_reconstruct_cartesian(zm_plan_t plan, const float* moments, int batch,
+                                        const zm_canvas_t* canvases, float* polar_tmp, unsigned flags,
+                                        void* stream) {
+    if (!plan || !moments || !polar_tmp) return set_error(ZM_EINVAL, "NULL argument");
+    int s = check_canvases(canvases, batch);
+    if (s != ZM_OK) return s;
+    if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
+    DeviceGuard g(plan->device);
+    s = launch_reconstruct(plan, moments, batch, polar_tmp, flags, (cudaStream_t)stream);
+    if (s != ZM_OK) return s;
+    return launch_polar_to_cart(plan, polar_tmp, batch, canvases, (cudaStream_t)stream);
+}
+
+extern "C" int zm_errors(zm_plan_t plan, const zm_image_t* ref, const zm_image_t* test, int batch, double* out,
+                         void* stream) {
+    if (!plan || !out) return set_error(ZM_EINVAL, "NULL argument");
+    int s = check_images(ref, batch);
+    if (s == ZM_OK) s = check_images(test, batch);
+    if (s != ZM_OK) return s;
+    for (int b = 0; b < batch; ++b)
+        if (ref[b].height != test[b].height || ref[b].width != test[b].width)
+            return set_error(ZM_EINVAL, "image %d: reference and test sizes differ", b);
+    DeviceGuard g(plan->device);
+    return launch_errors(plan, ref, test, nullptr, nullptr, batch, out, (cudaStream_t)stream);
+}
+
+extern "C" int zm_errors_polar(zm_plan_t plan, const float* fhat, const float* frec, int batch, double* out,
+                               void* stream) {
+    if (!plan || !fhat || !frec || !out) return set_error(ZM_EINVAL, "NULL argument");
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
+    DeviceGuard g(plan->device);
+    return launch_errors(plan, nullptr, nullptr, fhat, frec, batch, out, (cudaStream_t)stream);
+}
+
+extern "C" int zm_disk_minmax(zm_plan_t plan, const zm_image_t* imgs, int batch, float* out, void* stream) {
+    if (!plan || !out) return set_error(ZM_EINVAL, "NULL argument");
+    const int s = check_images(imgs, batch);
+    if (s != ZM_OK) return s;
+    DeviceGuard g(plan->device);
+    return launch_disk_minmax(plan, imgs, batch, out, (cudaStream_t)stream);
+}
+
+extern "C" int zm_minmax_normalize(zm_plan_t plan, const zm_canvas_t* canvases, int batch, const float* target,
+                                   void* stream) {
+    if (!plan || !target) return set_error(ZM_EINVAL, "NULL argument");
+    const int s = check_canvases(canvases, batch);
+    if (s != ZM_OK) return s;
+    DeviceGuard g(plan->device);
+    return launch_minmax_normalize(plan, canvases, batch, target, (cudaStream_t)stream);
+}

@@ -1,0 +1,161 @@
+// Internal declarations of the Zernike moment library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/zm.h"
+
+namespace zm {
+
+// ---------------------------------------------------------------- errors
+int set_error(int status, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define ZM_CUDA_TRY(expr)                                        \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return ::zm::cuda_error(_e, #expr); \
+    } while (0)
+
+#define ZM_LAUNCH_CHECK(what)                                    \
+    do {                                                         \
+        cudaError_t _e = cudaGetLastError();                     \
+        if (_e != cudaSuccess) return ::zm::cuda_error(_e, what); \
+        ::zm::count_launch();                                    \
+    } while (0)
+
+// Makes `dev` current for the lifetime of the guard and restores the caller's
+// device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------- index set
+// Stored pairs (n, m): m >= 0, n - m even, ordered by n then m (Sec. 2).
+inline int num_moments(int n_max) {
+    if (n_max < 0) return -1;
+    const int n = n_max + 1;               // off(n) of the next order
+    const int q = n / 2;
+    return (n % 2 == 0) ? q * (q + 1) : (q + 1) * (q + 1);
+}
+__host__ __device__ inline int moment_index(int n, int m) {
+    const int q = n / 2;
+    const int off = (n % 2 == 0) ? q * (q + 1) : (q + 1) * (q + 1);
+    return off + (m - (n & 1)) / 2;
+}
+
+// ---------------------------------------------------------------- FP64 table cache
+// One Eq. 7 table per (device, grid, N_rho), grown in n_max; plans hold a
+// reference, so a table outlives its cache slot while plans use it.
+struct ZrpTable {
+    int device = -1, grid = 0, n_rho = 0, n_max = -1, n_z = 0;
+    double* rho = nullptr;   // [n_rho] radial nodes
+    double* wr = nullptr;    // [n_rho] radial weights (Jacobian rho included)
+    double* R = nullptr;     // [P(n_max)][n_rho], moment order
+    float plan_ms = 0.f;     // time of the table build
+    ~ZrpTable();
+};
+int acquire_table(int device, int grid, int n_rho, int n_max, std::shared_ptr<ZrpTable>* out);
+
+// ---------------------------------------------------------------- plan
+enum Prec { PREC_FP32 = 0, PREC_BF16X3 = 1, PREC_FP16X3 = 2 };
+
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    int grow(size_t need);   // cudaMalloc on growth only (synchronous)
+    ~Workspace();
+};
+
+}  // namespace zm
+
+struct zm_plan_s {
+    int device = 0;
+    int n_max = 0, n_rho = 0, n_theta = 0, log_theta = 0, P = 0;
+    unsigned flags = 0;
+    int grid = 0, prec = 0;
+    std::shared_ptr<zm::ZrpTable> table;
+    // device constants of the plan
+    float* rho32 = nullptr;     // [n_rho]
+    float* A32 = nullptr;       // [P][n_rho], m-major rows: 2(n+1)/N_theta * wr_i * R_nm(rho_i)
+    float* R32m = nullptr;      // [P][n_rho], m-major rows: R_nm(rho_i) (reconstruction)
+    uint16_t* Ahi = nullptr;    // [P][n_rho], m-major: hi part of A (bf16 or fp16 bits)
+    uint16_t* Alo = nullptr;    // [P][n_rho], m-major: lo part of A
+    float a_scale = 1.f;        // Ahi/Alo hold A * a_scale (fp16 range); 1 for bf16
+    float2* tw = nullptr;       // [n_theta] e^{-2 pi i j / N_theta}
+    float2* cs = nullptr;       // [n_theta] (cos theta_k, sin theta_k)
+    int* mrow = nullptr;        // [n_max + 2] first m-major row of each m
+    int2* pair_nm = nullptr;    // [P] (n, m) of each moment index
+    std::vector<int> mrow_h;
+    // workspace (grown on demand)
+    zm::Workspace ws_F;         // ring spectra F[m][b][2][n_rho] (fp32)
+    zm::Workspace ws_part;      // split-K partial sums of the projection
+    zm::Workspace ws_G;         // reconstruction radial spectra G[b][m][2][n_rho]
+    zm::Workspace ws_red;       // reduction partials
+    zm::Workspace ws_scale;     // per-image spectrum scale (fp16 split)
+    // launch choices
+    int kb_rings = 8;           // rings per CTA in the resample + FFT kernel
+};
+
+namespace zm {
+
+// ---------------------------------------------------------------- launchers
+int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch,
+                   float* F, float* fhat_out, bool resample_only, cudaStream_t st);
+int launch_projection(zm_plan_t p, const float* F, int batch, float* out, unsigned flags,
+                      cudaStream_t st);
+void count_launch(int n = 1);
+int launch_reconstruct(zm_plan_t p, const float* moments, int batch, float* out,
+                       unsigned flags, cudaStream_t st);
+int launch_polar_to_cart(zm_plan_t p, const float* polar, int batch, const zm_canvas_t* cv,
+                         cudaStream_t st);
+int launch_errors(zm_plan_t p, const zm_image_t* ref, const zm_image_t* test,
+                  const float* fhat, const float* frec, int batch, double* out,
+                  cudaStream_t st);
+int launch_disk_minmax(zm_plan_t p, const zm_image_t* imgs, int batch, float* out,
+                       cudaStream_t st);
+int launch_minmax_normalize(zm_plan_t p, const zm_canvas_t* cv, int batch,
+                            const float* target, cudaStream_t st);
+int build_plan_tables(zm_plan_t p);
+
+// ---------------------------------------------------------------- shared device code
+struct GeoImage {          // device-side image descriptor (geometry resolved)
+    const float* data;
+    long long pitch;
+    int h, w;
+    float cx, cy, r;
+};
+
+inline GeoImage resolve(const zm_image_t& im) {
+    GeoImage g;
+    g.data = im.data;
+    g.pitch = im.pitch;
+    g.h = im.height;
+    g.w = im.width;
+    if (im.radius > 0.f) {
+        g.cx = im.cx; g.cy = im.cy; g.r = im.radius;
+    } else {
+        g.cx = 0.5f * (float)(im.width - 1);
+        g.cy = 0.5f * (float)(im.height - 1);
+        g.r = 0.5f * (float)(im.width < im.height ? im.width : im.height);
+    }
+    return g;
+}
+
+int check_images(const zm_image_t* imgs, int batch);
+
+}  // namespace zm

@@ -1,0 +1,261 @@
+"""ctypes binding of libzm.so (include/zm.h): the same entry points under the
+same names, doing argument marshalling only.
+
+Device buffers are passed as CUDA tensors (their data_ptr) or raw integer
+addresses; streams as torch.cuda.Stream, raw cudaStream_t integers or None
+(torch's current stream).  A failing call raises ZmError with the library's
+status and detail text.  Importing this module does not load the library;
+``lib()`` does and raises if ``libzm.so`` has not been built.
+"""
+
+import ctypes
+import os
+
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_longlong, c_uint, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libzm.so")
+
+ZM_OK, ZM_EINVAL, ZM_ENOMEM, ZM_ECUDA, ZM_ETIMEOUT, ZM_EUNSUPPORTED = range(6)
+ZM_GRID_MIDPOINT = 0x0
+ZM_GRID_GAUSS = 0x1
+ZM_PREC_FP32 = 0x00
+ZM_PREC_BF16X3 = 0x10
+ZM_PREC_FP16X3 = 0x20
+ZM_NEUMANN = 0x1
+
+
+class ZmError(RuntimeError):
+    def __init__(self, status, detail):
+        super().__init__("zm status %d (%s): %s" % (status, _STATUS.get(status, "?"), detail))
+        self.status = status
+
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timed out",
+           5: "unsupported"}
+
+
+class zm_image_t(ctypes.Structure):
+    _fields_ = [("data", c_void_p), ("height", c_int), ("width", c_int), ("pitch", c_longlong),
+                ("cx", c_float), ("cy", c_float), ("radius", c_float)]
+
+
+class zm_canvas_t(ctypes.Structure):
+    _fields_ = [("data", c_void_p), ("height", c_int), ("width", c_int), ("pitch", c_longlong),
+                ("cx", c_float), ("cy", c_float), ("radius", c_float)]
+
+
+# name -> (restype, argtypes); mirrors include/zm.h
+SIGNATURES = {
+    "zm_num_moments": (c_int, [c_int]),
+    "zm_index": (c_int, [c_int, c_int]),
+    "zm_strerror": (c_char_p, [c_int]),
+    "zm_last_error": (c_char_p, []),
+    "zm_plan": (c_int, [POINTER(c_void_p), c_int, c_int, c_int, c_uint]),
+    "zm_plan_destroy": (c_int, [c_void_p]),
+    "zm_plan_reserve": (c_int, [c_void_p, c_int]),
+    "zm_plan_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                             POINTER(c_uint)]),
+    "zm_plan_table": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "zm_plan_nodes": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "zm_moments": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_uint, c_void_p]),
+    "zm_moments_ex": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_uint, c_void_p]),
+    "zm_moments_polar": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_resample": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
+    "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
+    "zm_project": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_launch_count": (ctypes.c_ulonglong, []),
+    "zm_reconstruct": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_reconstruct_cartesian": (c_int, [c_void_p, c_void_p, c_int, POINTER(zm_canvas_t), c_void_p, c_uint,
+                                         c_void_p]),
+    "zm_errors": (c_int, [c_void_p, POINTER(zm_image_t), POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
+    "zm_errors_polar": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "zm_disk_minmax": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
+    "zm_minmax_normalize": (c_int, [c_void_p, POINTER(zm_canvas_t), c_int, c_void_p, c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libzm.so once; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libzm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != ZM_OK:
+        raise ZmError(status, lib().zm_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError("cannot take a device pointer of %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _geometry(g):
+    if g is None:
+        return 0.0, 0.0, -1.0
+    return float(g[0]), float(g[1]), float(g[2])
+
+
+def image_desc(t, geometry=None):
+    """zm_image_t for a 2-D float32 CUDA tensor (rows may be strided)."""
+    if t.dim() != 2 or t.dtype.__str__() != "torch.float32" or not t.is_cuda or t.stride(1) != 1:
+        raise ValueError("images must be 2-D float32 CUDA tensors with unit column stride")
+    cx, cy, r = _geometry(geometry)
+    return zm_image_t(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), cx, cy, r)
+
+
+def canvas_desc(t, geometry=None):
+    d = image_desc(t, geometry)
+    return zm_canvas_t(d.data, d.height, d.width, d.pitch, d.cx, d.cy, d.radius)
+
+
+def _images(imgs, geometries=None):
+    imgs = list(imgs)
+    geos = list(geometries) if geometries is not None else [None] * len(imgs)
+    arr = (zm_image_t * len(imgs))(*[image_desc(t, g) for t, g in zip(imgs, geos)])
+    return arr, len(imgs)
+
+
+def _canvases(cvs, geometries=None):
+    cvs = list(cvs)
+    geos = list(geometries) if geometries is not None else [None] * len(cvs)
+    arr = (zm_canvas_t * len(cvs))(*[canvas_desc(t, g) for t, g in zip(cvs, geos)])
+    return arr, len(cvs)
+
+
+# ------------------------------------------------------------------ entry points
+def zm_num_moments(n_max):
+    return lib().zm_num_moments(n_max)
+
+
+def zm_index(n, m):
+    return lib().zm_index(n, m)
+
+
+def zm_strerror(status):
+    return lib().zm_strerror(status).decode()
+
+
+def zm_last_error():
+    return lib().zm_last_error().decode()
+
+
+def zm_plan(n_max, n_rho, n_theta, flags=0):
+    h = c_void_p()
+    _check(lib().zm_plan(ctypes.byref(h), n_max, n_rho, n_theta, flags))
+    return h.value
+
+
+def zm_plan_destroy(plan):
+    _check(lib().zm_plan_destroy(plan))
+
+
+def zm_plan_reserve(plan, batch):
+    _check(lib().zm_plan_reserve(plan, batch))
+
+
+def zm_plan_info(plan):
+    a, b, c, d, f = c_int(), c_int(), c_int(), c_int(), c_uint()
+    _check(lib().zm_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                              ctypes.byref(f)))
+    return {"n_max": a.value, "n_rho": b.value, "n_theta": c.value, "num_moments": d.value, "flags": f.value}
+
+
+def zm_plan_table(plan, dst, stream=None):
+    _check(lib().zm_plan_table(plan, _ptr(dst), _stream(stream)))
+
+
+def zm_plan_nodes(plan, rho=None, wr=None, stream=None):
+    _check(lib().zm_plan_nodes(plan, _ptr(rho), _ptr(wr), _stream(stream)))
+
+
+def zm_moments(plan, images, out, flags=0, stream=None, geometries=None):
+    arr, n = _images(images, geometries)
+    _check(lib().zm_moments(plan, arr, n, _ptr(out), flags, _stream(stream)))
+
+
+def zm_moments_ex(plan, images, out, fhat=None, flags=0, stream=None, geometries=None):
+    arr, n = _images(images, geometries)
+    _check(lib().zm_moments_ex(plan, arr, n, _ptr(out), _ptr(fhat), flags, _stream(stream)))
+
+
+def zm_moments_polar(plan, fhat, batch, out, flags=0, stream=None):
+    _check(lib().zm_moments_polar(plan, _ptr(fhat), batch, _ptr(out), flags, _stream(stream)))
+
+
+def zm_resample(plan, images, fhat, stream=None, geometries=None):
+    arr, n = _images(images, geometries)
+    _check(lib().zm_resample(plan, arr, n, _ptr(fhat), _stream(stream)))
+
+
+def zm_ring_spectra(plan, images, spectra, fhat=None, stream=None, geometries=None):
+    arr, n = _images(images, geometries)
+    _check(lib().zm_ring_spectra(plan, arr, n, _ptr(spectra), _ptr(fhat), _stream(stream)))
+
+
+def zm_project(plan, spectra, batch, out, flags=0, stream=None):
+    _check(lib().zm_project(plan, _ptr(spectra), batch, _ptr(out), flags, _stream(stream)))
+
+
+def zm_launch_count():
+    return int(lib().zm_launch_count())
+
+
+def zm_reconstruct(plan, moments, batch, out, flags=0, stream=None):
+    _check(lib().zm_reconstruct(plan, _ptr(moments), batch, _ptr(out), flags, _stream(stream)))
+
+
+def zm_reconstruct_cartesian(plan, moments, canvases, polar_tmp, flags=0, stream=None, geometries=None):
+    arr, n = _canvases(canvases, geometries)
+    _check(lib().zm_reconstruct_cartesian(plan, _ptr(moments), n, arr, _ptr(polar_tmp), flags, _stream(stream)))
+
+
+def zm_errors(plan, ref, test, out, stream=None, geometries=None):
+    ra, n = _images(ref, geometries)
+    ta, n2 = _images(test, geometries)
+    if n != n2:
+        raise ValueError("reference and test batches differ")
+    _check(lib().zm_errors(plan, ra, ta, n, _ptr(out), _stream(stream)))
+
+
+def zm_errors_polar(plan, fhat, frec, batch, out, stream=None):
+    _check(lib().zm_errors_polar(plan, _ptr(fhat), _ptr(frec), batch, _ptr(out), _stream(stream)))
+
+
+def zm_disk_minmax(plan, images, out, stream=None, geometries=None):
+    arr, n = _images(images, geometries)
+    _check(lib().zm_disk_minmax(plan, arr, n, _ptr(out), _stream(stream)))
+
+
+def zm_minmax_normalize(plan, canvases, target, stream=None, geometries=None):
+    arr, n = _canvases(canvases, geometries)
+    _check(lib().zm_minmax_normalize(plan, arr, n, _ptr(target), _stream(stream)))

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every entry point the header
+declares; host-only helpers agree with the oracle's index set (CPU)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import zernike
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "zm.h")
+
+
+@pytest.fixture(scope="module")
+def zm():
+    from paper_2304_14492_gb300 import build as b
+    from paper_2304_14492_gb300 import native
+    b.build()
+    native.lib()
+    return native
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9 \*]*?\b(zm_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("zm_plan", "zm_moments", "zm_reconstruct", "zm_plan_destroy", "zm_strerror",
+                     "zm_num_moments", "zm_index", "zm_moments_polar"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(zm):
+    L = ctypes.CDLL(zm.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+        assert name in zm.SIGNATURES, name
+    assert set(zm.SIGNATURES) == set(declared_functions())
+
+
+def test_index_helpers_match_oracle(zm):
+    for n_max in range(0, 60):
+        assert zm.zm_num_moments(n_max) == zernike.num_moments(n_max)
+    for row, (n, m) in enumerate(zernike.index_pairs(40)):
+        assert zm.zm_index(n, m) == row
+    assert zm.zm_index(3, 2) == -1 and zm.zm_index(2, 4) == -1 and zm.zm_index(-1, 0) == -1
+    assert zm.zm_num_moments(-1) == -1
+    assert zm.zm_strerror(0) == "ok" and zm.zm_strerror(1) == "invalid argument"
+
+
+def test_plan_argument_errors_are_reported_not_raised(zm):
+    # argument validation happens before any device call
+    for args in [(-1, 8, 8), (4, 0, 16), (4, 8, 12), (10, 8, 16), (4, 8, 4096)]:
+        with pytest.raises(zm.ZmError) as e:
+            zm.zm_plan(*args)
+        assert e.value.status in (zm.ZM_EINVAL, zm.ZM_EUNSUPPORTED)
+    with pytest.raises(zm.ZmError):
+        zm.zm_plan(4, 8, 16, 0x2)          # unknown grid flag
+
+
+def test_no_gpu_plan_fails_cleanly(zm):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(zm.ZmError) as e:
+        zm.zm_plan(4, 8, 16)
+    assert e.value.status == zm.ZM_ECUDA

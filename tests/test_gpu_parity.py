@@ -1,0 +1,359 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the
+C ABI (run with -m gpu on a GB300).
+
+Bars: the FP64 table of Eq. 7 within 1e-12 of the oracle's recurrence (and a
+Gram matrix within 1e-10 of diag 1/(2(n+1)) on Gauss-Legendre nodes); FP32
+moments within 1e-4 * max|Z| of the oracle (the stated tolerance); component
+stages within bounds derived from FP32 rounding of their inputs.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import grid, metrics, moments as om, reconstruct as orc, resample, zernike  # noqa: E402
+from paper_2304_14492_gb300 import native as zm, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+TOL_Z = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2304_14492_gb300.build import build
+    build()
+    zm.lib()
+
+
+class Plan:
+    def __init__(self, n_max, n_rho, n_theta, flags=0):
+        self.h = zm.zm_plan(n_max, n_rho, n_theta, flags)
+        self.n_max, self.n_rho, self.n_theta = n_max, n_rho, n_theta
+        self.P = zm.zm_num_moments(n_max)
+        self.grid = "gauss" if flags & zm.ZM_GRID_GAUSS else "midpoint"
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        zm.zm_plan_destroy(self.h)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+def as_complex(out):
+    o = out.double().cpu().numpy()
+    return o[..., 0] + 1j * o[..., 1]
+
+
+def gpu_moments(plan, imgs, flags=0, geometries=None):
+    ts = [dev(i) for i in imgs]
+    out = torch.empty((len(ts), plan.P, 2), device=DEV)
+    zm.zm_moments(plan.h, ts, out, flags, geometries=geometries)
+    torch.cuda.synchronize()
+    return as_complex(out)
+
+
+def oracle_moments(img, plan, neumann=False, geometry=None):
+    return om.moments(np.asarray(img, np.float32).astype(np.float64), plan.n_max, plan.n_rho, plan.n_theta,
+                      grid=plan.grid, neumann=neumann, geometry=geometry)
+
+
+# ------------------------------------------------------------------ a1: Eq. 7 table
+@pytest.mark.parametrize("n_max,n_rho,n_theta,flags", [
+    (20, 32, 64, 0), (50, 256, 256, 0), (100, 1024, 1024, 0), (0, 1, 8, 0),
+    (13, 37, 32, zm.ZM_GRID_GAUSS), (200, 202, 512, zm.ZM_GRID_GAUSS)])
+def test_table_eq7_matches_recurrence(n_max, n_rho, n_theta, flags):
+    with Plan(n_max, n_rho, n_theta, flags) as p:
+        R = torch.empty((p.P, n_rho), device=DEV, dtype=torch.float64)
+        rho = torch.empty(n_rho, device=DEV, dtype=torch.float64)
+        wr = torch.empty(n_rho, device=DEV, dtype=torch.float64)
+        zm.zm_plan_table(p.h, R)
+        zm.zm_plan_nodes(p.h, rho, wr)
+        torch.cuda.synchronize()
+        R, rho, wr = R.cpu().numpy(), rho.cpu().numpy(), wr.cpu().numpy()
+    rho_o, wr_o = grid.radial_nodes(n_rho, p.grid)
+    assert np.max(np.abs(rho - rho_o)) <= 1e-14
+    assert np.max(np.abs(wr - wr_o)) <= 1e-14 * max(1.0, np.max(np.abs(wr_o))) + 1e-16
+    ref = zernike.zrp_table(n_max, rho_o)
+    assert np.max(np.abs(R - ref)) <= 1e-12
+    if flags & zm.ZM_GRID_GAUSS and n_rho >= n_max + 1:
+        pairs = zernike.index_pairs(n_max)
+        worst = 0.0
+        for m in range(n_max + 1):
+            rows = [r for r, (n, mm) in enumerate(pairs) if mm == m]
+            ns = np.array([pairs[r][0] for r in rows])
+            G = (R[rows] * wr) @ R[rows].T
+            worst = max(worst, np.max(np.abs(G - np.diag(1.0 / (2.0 * (ns + 1))))))
+        assert worst <= 1e-10, worst
+
+
+# ------------------------------------------------------------------ a2: resampling
+@pytest.mark.parametrize("shape,n_rho,n_theta,geometry", [
+    ((64, 64), 32, 64, None), ((45, 70), 21, 32, None), ((50, 40), 17, 64, (10.25, 30.5, 28.0))])
+def test_resample_matches_oracle(shape, n_rho, n_theta, geometry):
+    img = synth.uniform_image(*shape, workload=11, index=0)
+    with Plan(4, n_rho, n_theta) as p:
+        f = torch.empty((1, n_rho, n_theta), device=DEV)
+        zm.zm_resample(p.h, [dev(img)], f, geometries=[geometry] if geometry else None)
+        torch.cuda.synchronize()
+    rho, _ = grid.radial_nodes(n_rho)
+    ref = resample.polar_resample(img.astype(np.float64), rho, n_theta, geometry)
+    assert np.max(np.abs(f[0].double().cpu().numpy() - ref)) <= 2e-5
+
+
+def test_resample_strided_rows():
+    big = synth.uniform_image(80, 100, workload=12, index=0)
+    t = dev(big)[5:69, 10:74]                          # 64 x 64 view, pitch 100
+    img = big[5:69, 10:74]
+    with Plan(4, 32, 64) as p:
+        f = torch.empty((1, 32, 64), device=DEV)
+        zm.zm_resample(p.h, [t], f)
+        torch.cuda.synchronize()
+    rho, _ = grid.radial_nodes(32)
+    ref = resample.polar_resample(img.astype(np.float64), rho, 64)
+    assert np.max(np.abs(f[0].double().cpu().numpy() - ref)) <= 2e-5
+
+
+# ------------------------------------------------------------------ a3: ring spectra
+@pytest.mark.parametrize("n_max,n_rho,n_theta", [(20, 32, 64), (3, 9, 8), (13, 37, 32), (100, 64, 1024),
+                                                 (300, 16, 1024), (500, 8, 2048)])
+def test_ring_spectra_match_direct_dft(n_max, n_rho, n_theta):
+    img = synth.uniform_image(2 * n_rho + 3, 2 * n_rho + 1, workload=13, index=n_max)
+    with Plan(n_max, n_rho, n_theta) as p:
+        F = torch.empty((n_max + 1, 1, 2, n_rho), device=DEV)
+        fh = torch.empty((1, n_rho, n_theta), device=DEV)
+        zm.zm_ring_spectra(p.h, [dev(img)], F, fh)
+        torch.cuda.synchronize()
+    Fg = F[:, 0, 0, :].double().cpu().numpy() + 1j * F[:, 0, 1, :].double().cpu().numpy()   # [m][i]
+    ref = om.angular_dft(fh[0].double().cpu().numpy(), n_max)                               # [i][m]
+    assert np.max(np.abs(Fg.T - ref)) <= 2e-6 * np.max(np.abs(ref)) * np.log2(n_theta)
+
+
+# ------------------------------------------------------------------ a3-a5 on polar input
+@pytest.mark.parametrize("npr,mpr", [(0, 0), (6, 2), (11, 5), (24, 24), (30, 12)])
+def test_polar_zernike_input_closed_form(npr, mpr):
+    n_max, n_theta = 30, 64
+    n_rho = n_max + 1
+    rho, _ = grid.radial_nodes(n_rho, "gauss")
+    th = grid.angles(n_theta)
+    R = zernike.zrp_table(npr, rho)[zernike.moment_index(npr, mpr)]
+    fc = R[:, None] * np.cos(mpr * th)[None, :]
+    fs = R[:, None] * np.sin(mpr * th)[None, :]
+    with Plan(n_max, n_rho, n_theta, zm.ZM_GRID_GAUSS) as p:
+        fh = dev(np.stack([fc, fs]))
+        out = torch.empty((2, p.P, 2), device=DEV)
+        zm.zm_moments_polar(p.h, fh, 2, out)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+    k = zernike.moment_index(npr, mpr)
+    want = np.zeros(p.P, complex)
+    want[k] = 1.0 if mpr == 0 else 0.5
+    assert np.max(np.abs(Z[0] - want)) <= 1e-5
+    if mpr > 0:
+        want[k] = -0.5j
+        assert np.max(np.abs(Z[1] - want)) <= 1e-5
+
+
+def test_moments_polar_matches_oracle():
+    rng = np.random.default_rng(3)
+    n_max, n_rho, n_theta = 25, 40, 64
+    fh = rng.random((3, n_rho, n_theta)).astype(np.float32)
+    with Plan(n_max, n_rho, n_theta) as p:
+        out = torch.empty((3, p.P, 2), device=DEV)
+        zm.zm_moments_polar(p.h, dev(fh), 3, out, zm.ZM_NEUMANN)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+    for b in range(3):
+        ref = om.moments_polar(fh[b].astype(np.float64), n_max, neumann=True)
+        assert metrics.rel_max_err(Z[b], ref) <= TOL_Z
+
+
+# ------------------------------------------------------------------ a2-a5 end to end
+@pytest.mark.parametrize("neumann", [False, True])
+def test_moments_uniform_64(neumann):
+    # 64x64 U[0,1] image, n_max 20, 32 x 64 grid
+    img = synth.uniform_image(64, 64, workload=0, index=0)
+    with Plan(20, 32, 64) as p:
+        Z = gpu_moments(p, [img], zm.ZM_NEUMANN if neumann else 0)[0]
+        ref = oracle_moments(img, p, neumann=neumann)
+    assert metrics.rel_max_err(Z, ref) <= TOL_Z
+
+
+def test_moments_blob_batch_512():
+    # 16 blob images of 512x512, n_max 50, 256 x 256 grid
+    imgs = [synth.blob_image(512, 512, 8, workload=1, index=b) for b in range(16)]
+    with Plan(50, 256, 256) as p:
+        Z = gpu_moments(p, imgs)
+        for b in range(16):
+            assert metrics.rel_max_err(Z[b], oracle_moments(imgs[b], p)) <= TOL_Z
+
+
+def test_moments_ragged_and_uneven():
+    # ragged ring blocks (N_rho = 37), odd n_max, N_theta = next pow2 >= 2 n_max + 2,
+    # images of different sizes and geometries in one batch
+    imgs = [synth.uniform_image(45, 70, workload=2, index=0), synth.uniform_image(33, 33, workload=2, index=1),
+            synth.blob_image(90, 60, 3, workload=2, index=2)]
+    geos = [None, (16.0, 16.0, 16.0), (20.5, 40.25, 35.0)]
+    with Plan(13, 37, 32) as p:
+        Z = gpu_moments(p, imgs, geometries=[g if g else (0, 0, -1) for g in geos])
+        for b in range(3):
+            assert metrics.rel_max_err(Z[b], oracle_moments(imgs[b], p, geometry=geos[b])) <= TOL_Z
+
+
+def test_moments_batch_spanning_launches_and_order_independence():
+    imgs = [synth.uniform_image(16, 16, workload=4, index=b) for b in range(130)]
+    with Plan(5, 8, 16) as p:
+        Z = gpu_moments(p, imgs)
+        alone = gpu_moments(p, [imgs[129]])[0]
+        for b in (0, 64, 127, 128, 129):
+            assert metrics.rel_max_err(Z[b], oracle_moments(imgs[b], p)) <= TOL_Z
+    assert np.max(np.abs(alone - Z[129])) <= 1e-6 * np.max(np.abs(alone))
+
+
+@pytest.mark.parametrize("n_max,n_rho,n_theta,shape", [(0, 1, 8, (4, 4)), (1, 2, 8, (1, 1)), (3, 5, 8, (8, 8)),
+                                                        (127, 64, 256, (128, 128)), (511, 32, 1024, (64, 64)),
+                                                        (1023, 8, 2048, (16, 16))])
+def test_moments_edge_sizes(n_max, n_rho, n_theta, shape):
+    img = synth.uniform_image(*shape, workload=5, index=n_max)
+    with Plan(n_max, n_rho, n_theta) as p:
+        Z = gpu_moments(p, [img])[0]
+        ref = oracle_moments(img, p)
+    assert metrics.rel_max_err(Z, ref) <= TOL_Z
+
+
+def test_moments_gauss_grid_and_constant_image():
+    img = np.ones((64, 64), np.float32)
+    with Plan(20, 24, 64, zm.ZM_GRID_GAUSS) as p:
+        Z = gpu_moments(p, [img], geometries=[(31.5, 31.5, 30.0)])[0]
+    assert abs(Z[0] - 1.0) <= 1e-6
+    assert np.max(np.abs(Z[1:])) <= 1e-6
+
+
+def test_rotation_invariance_on_gpu():
+    img = synth.blob_image(128, 128, 6, workload=6, index=0)
+    with Plan(30, 64, 128) as p:
+        Z = gpu_moments(p, [img, np.rot90(img).copy()])
+    ms = np.array([m for _, m in zernike.index_pairs(30)])
+    assert np.max(np.abs(Z[1] - (-1j) ** ms * Z[0])) <= 1e-5 * np.max(np.abs(Z[0]))
+
+
+def test_deterministic():
+    img = synth.blob_image(256, 256, 6, workload=7, index=0)
+    with Plan(40, 128, 128) as p:
+        a = gpu_moments(p, [img, img])
+        b = gpu_moments(p, [img, img])
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ a6: reconstruction
+@pytest.mark.parametrize("neumann", [False, True])
+@pytest.mark.parametrize("n_max,n_rho,n_theta", [(20, 32, 64), (13, 37, 32), (100, 128, 256), (0, 3, 8)])
+def test_reconstruct_polar_matches_oracle(neumann, n_max, n_rho, n_theta):
+    img = synth.uniform_image(2 * n_rho, 2 * n_rho, workload=8, index=n_max)
+    with Plan(n_max, n_rho, n_theta) as p:
+        Zref = oracle_moments(img, p)
+        zin = dev(np.stack([Zref.real, Zref.imag], -1)[None])
+        out = torch.empty((1, n_rho, n_theta), device=DEV)
+        zm.zm_reconstruct(p.h, zin, 1, out, zm.ZM_NEUMANN if neumann else 0)
+        torch.cuda.synchronize()
+    ref = orc.reconstruct_polar(Zref.astype(np.complex64).astype(np.complex128), n_max, n_rho, n_theta,
+                                neumann=neumann)
+    assert np.max(np.abs(out[0].double().cpu().numpy() - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_reconstruct_cartesian_matches_oracle():
+    h, w = 60, 75
+    img = synth.blob_image(h, w, 4, workload=9, index=0)
+    n_max, n_rho, n_theta = 24, 30, 64
+    with Plan(n_max, n_rho, n_theta) as p:
+        Zref = oracle_moments(img, p)
+        zin = dev(np.stack([Zref.real, Zref.imag], -1)[None])
+        canvas = torch.full((h, w), 7.0, device=DEV)
+        polar = torch.empty((1, n_rho, n_theta), device=DEV)
+        zm.zm_reconstruct_cartesian(p.h, zin, [canvas], polar, zm.ZM_NEUMANN)
+        torch.cuda.synchronize()
+    rho, _ = grid.radial_nodes(n_rho)
+    fp = orc.reconstruct_polar(Zref, n_max, n_rho, n_theta, neumann=True)
+    ref = orc.polar_to_cartesian(fp, rho, h, w)
+    geo = grid.default_geometry(h, w)
+    y, x = np.mgrid[0:h, 0:w]
+    r_xy, _ = grid.pixel_to_polar(x, y, geo)
+    sel = np.abs(r_xy - 1.0) > 1e-5
+    got = canvas.double().cpu().numpy()
+    assert np.max(np.abs(got[sel] - ref[sel])) <= 1e-4 * np.max(np.abs(ref))
+    assert np.all(got[r_xy > 1.0 + 1e-5] == 0.0)
+
+
+# ------------------------------------------------------------------ a7: errors and min-max
+def test_errors_and_minmax_match_oracle():
+    h, w = 70, 64
+    f = synth.blob_image(h, w, 5, workload=10, index=0)
+    g = f + synth.uniform_image(h, w, workload=10, index=1) * 0.1
+    mask = metrics.disk_mask(h, w)
+    with Plan(4, 8, 16) as p:
+        out = torch.empty((1, 4), device=DEV, dtype=torch.float64)
+        zm.zm_errors(p.h, [dev(f)], [dev(g)], out)
+        mm = torch.empty((1, 2), device=DEV)
+        zm.zm_disk_minmax(p.h, [dev(f)], mm)
+        cv = dev(g)
+        target = torch.tensor([[0.0, 255.0]], device=DEV)
+        zm.zm_minmax_normalize(p.h, [cv], target)
+        fr = torch.empty((1, 8, 16), device=DEV)
+        fr2 = torch.empty((1, 8, 16), device=DEV)
+        zm.zm_resample(p.h, [dev(f)], fr)
+        zm.zm_resample(p.h, [dev(g)], fr2)
+        outp = torch.empty((1, 4), device=DEV, dtype=torch.float64)
+        zm.zm_errors_polar(p.h, fr, fr2, 1, outp)
+        torch.cuda.synchronize()
+    o = out[0].cpu().numpy()
+    assert abs(o[0] - metrics.eps1(f, g, mask)) <= 1e-4 * metrics.eps1(f, g, mask)
+    assert abs(o[1] - metrics.eps13(f, g, mask)) <= 1e-4 * metrics.eps13(f, g, mask)
+    assert o[3] == mask.sum()
+    m = mm[0].cpu().numpy()
+    assert abs(m[0] - f[mask].min()) <= 1e-7 and abs(m[1] - f[mask].max()) <= 1e-7
+    ref = metrics.minmax_normalize(g.astype(np.float64), 0.0, 255.0, mask)
+    got = cv.double().cpu().numpy()
+    assert np.max(np.abs(got[mask] - ref[mask])) <= 1e-3
+    assert np.array_equal(got[~mask], g[~mask])
+    a, b = fr[0].double().cpu().numpy(), fr2[0].double().cpu().numpy()
+    op = outp[0].cpu().numpy()
+    assert abs(op[0] - np.sum((a - b) ** 2) / np.sum(a ** 2)) <= 1e-4 * op[0]
+    assert abs(op[1] - np.sum((a - b) ** 2) / (a.max() ** 2 * a.size)) <= 1e-4 * op[1]
+
+
+# ------------------------------------------------------------------ argument errors
+def test_argument_errors_on_gpu():
+    with Plan(4, 8, 16) as p:
+        x = dev(np.zeros((8, 8)))
+        out = torch.empty((1, p.P, 2), device=DEV)
+        with pytest.raises(zm.ZmError) as e:
+            zm.zm_moments(p.h, [x], out, flags=0x80)
+        assert e.value.status == zm.ZM_EINVAL
+        with pytest.raises(zm.ZmError):
+            zm.zm_moments(p.h, [], out)
+        assert zm.lib().zm_moments(p.h, None, 1, out.data_ptr(), 0, None) == zm.ZM_EINVAL
+        assert zm.lib().zm_reconstruct(p.h, None, 1, out.data_ptr(), 0, None) == zm.ZM_EINVAL
+
+
+# ------------------------------------------------------------------ full size (4K, bench launch shape)
+def test_4k_bench_configuration_sampled():
+    # 3840x2160 blob frames, n_max 100, 1024 x 1024 grid, batch 16 as timed by
+    # the benchmark; images 0 and 15 are checked in full against the oracle.
+    B = 16
+    imgs = [synth.blob_image(2160, 3840, 32, workload=2, index=b) for b in (0, 15)]
+    others = [torch.rand((2160, 3840), device=DEV) for _ in range(B - 2)]
+    with Plan(100, 1024, 1024) as p:
+        ts = [dev(imgs[0])] + others + [dev(imgs[1])]
+        out = torch.empty((B, p.P, 2), device=DEV)
+        zm.zm_moments(p.h, ts, out)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+        for b, img in ((0, imgs[0]), (B - 1, imgs[1])):
+            assert metrics.rel_max_err(Z[b], oracle_moments(img, p)) <= TOL_Z
