@@ -14,6 +14,8 @@
  *  - Image, moment and output buffers are DEVICE pointers owned by the caller
  *    (e.g. the data_ptr() of a CUDA tensor).  The descriptor arrays
  *    (zm_image_t / zm_canvas_t) are HOST arrays read during the call.
+ *  - Moment buffers and polar reconstruction outputs must be 8-byte aligned
+ *    (they are accessed as float pairs); ZM_EINVAL otherwise.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued asynchronously on it; results are valid once the stream
  *    has been synchronised.  A plan may be used from one stream at a time.
@@ -112,6 +114,11 @@ int zm_plan_destroy(zm_plan_t plan);
 /* Grow the plan's workspace so that later calls with batch <= `batch`
  * allocate nothing (e.g. before CUDA graph capture).  Synchronous. */
 int zm_plan_reserve(zm_plan_t plan, int batch);
+
+/* Synchronise the device, then report ZM_ETIMEOUT if any kernel of this plan
+ * gave up a bounded wait since the previous call (and clear that flag);
+ * ZM_OK otherwise. */
+int zm_plan_status(zm_plan_t plan);
 
 /* Plan parameters; any output pointer may be NULL. */
 int zm_plan_info(zm_plan_t plan, int* n_max, int* n_rho, int* n_theta,

@@ -348,6 +348,8 @@ int build_plan_tables(zm_plan_t p) {
     ZM_CUDA_TRY(cudaMalloc(&p->tw, sizeof(float2) * p->n_theta));
     ZM_CUDA_TRY(cudaMalloc(&p->cs, sizeof(float2) * p->n_theta));
     ZM_CUDA_TRY(cudaMalloc(&p->mrow, sizeof(int) * (p->n_max + 2)));
+    ZM_CUDA_TRY(cudaMalloc(&p->status, sizeof(int)));
+    ZM_CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
     ZM_CUDA_TRY(cudaMalloc(&p->pair_nm, sizeof(int2) * P));
     ZM_CUDA_TRY(cudaMemcpy(p->mrow, p->mrow_h.data(), sizeof(int) * (p->n_max + 2), cudaMemcpyHostToDevice));
     ZM_CUDA_TRY(cudaMemcpy(p->pair_nm, pairs.data(), sizeof(int2) * P, cudaMemcpyHostToDevice));
@@ -392,6 +394,7 @@ static void free_plan(zm_plan_t p) {
     cudaFree(p->cs);
     cudaFree(p->mrow);
     cudaFree(p->pair_nm);
+    cudaFree(p->status);
     delete p;
 }
 
@@ -470,6 +473,19 @@ extern "C" int zm_plan_destroy(zm_plan_t plan) {
     DeviceGuard g(plan->device);
     cudaDeviceSynchronize();
     free_plan(plan);
+    return ZM_OK;
+}
+
+extern "C" int zm_plan_status(zm_plan_t plan) {
+    if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
+    DeviceGuard g(plan->device);
+    ZM_CUDA_TRY(cudaDeviceSynchronize());
+    int st = 0;
+    ZM_CUDA_TRY(cudaMemcpy(&st, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        ZM_CUDA_TRY(cudaMemset(plan->status, 0, sizeof(int)));
+        return set_error(st, "a kernel of this plan gave up a bounded wait");
+    }
     return ZM_OK;
 }
 

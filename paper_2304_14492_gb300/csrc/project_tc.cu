@@ -1,12 +1,397 @@
-// Radial projection on the tensor cores (bf16 / fp16 hi+lo split, FP32
-// accumulate).
+// Radial projection of Eq. 1 on the 5th-generation tensor cores.
+//
+// For each repetition m the projection is the contraction
+//   D[col][n] = sum_i F_m[col][i] A_m[n][i],   col = 2b + re/im,
+// with A_m[n][i] = (n+1)/pi * wr_i * 2pi/N_theta * R_nm(rho_i).  Both operands
+// are split into a high and a low 16-bit part (bf16 or fp16): x = x_hi + x_lo,
+// and the product is accumulated in FP32 as F_hi A_hi + F_hi A_lo + F_lo A_hi
+// (the dropped F_lo A_lo term is below the FP32 rounding of the sum).
+//
+// One CTA = one m, 128 image columns (the MMA's M), all K_m orders (the MMA's
+// N, padded to a multiple of 16) and one slice of the radial index i (the
+// reduction, split over CTAs and summed by k_project_reduce).  Per 64-wide
+// chunk of i: the 128 threads load F (fp32), split it and store both halves in
+// the K-major, no-swizzle canonical layout (8-row x 16-byte core matrices;
+// core matrices adjacent in K are LBO = 128 B apart, 8-row groups SBO = 1024 B
+// apart); the precomputed A halves are copied in the same layout; one thread
+// issues 4 k-steps x 3 tcgen05.mma (kind::f16, cta_group::1) into a TMEM
+// accumulator and commits them to an mbarrier.  The epilogue reads TMEM with
+// tcgen05.ld (warp w owns lanes 32w..32w+31 = columns of D's M dimension).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
 #include "zm_internal.cuh"
 
 namespace zm {
 
+constexpr int TC_M = 128;            // image columns per CTA (MMA M)
+constexpr int TC_KC = 64;            // radial nodes per chunk
+constexpr int TC_THREADS = 128;
+constexpr int TC_NMAX = 256;         // orders per CTA (MMA N upper bound)
+constexpr int TC_FTILE = TC_M * TC_KC * 2;          // bytes of one 16-bit F tile
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s bound on any wait
+
+struct TcParams {
+    const float* F;          // [n_max+1][ncol][n_rho]
+    const uint16_t* Ahi;     // [P][n_rho] m-major rows
+    const uint16_t* Alo;
+    const int* mrow;
+    float* part;             // [S][P][ncol]
+    int* status;             // device status word (ZM_ETIMEOUT on a timed-out wait)
+    int n_max, n_rho, ncol, P, chunk;
+    int ntmax;               // A tile rows reserved in shared memory (widest N of the launch)
+    int fp16;                // 0: bf16 halves, 1: fp16 halves (scaled)
+    float a_scale;           // A halves hold A * a_scale
+    const unsigned* colmax;  // fp16: per column max |F| (float bits); NULL = no scaling
+};
+
+// Power-of-two scale putting a column's largest |F| just below 2^14, so the
+// fp16 halves neither overflow nor lose the low part to subnormals.
+__device__ __forceinline__ float column_scale(const unsigned* colmax, int col) {
+    if (!colmax) return 1.f;
+    const float mx = __uint_as_float(colmax[col]);
+    if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+    int e;
+    frexpf(mx, &e);
+    return ldexpf(1.f, 14 - e);
+}
+
+// max |F[m][col][i]| over m and i, per column, as ordered float bits.
+__global__ void k_colmax(const float* __restrict__ F, int nm1, int ncol, int n_rho, unsigned* __restrict__ out) {
+    const int col = blockIdx.x;
+    float mx = 0.f;
+    for (int e = threadIdx.x + blockIdx.y * blockDim.x; e < nm1 * n_rho; e += blockDim.x * gridDim.y) {
+        const int m = e / n_rho, i = e - m * n_rho;
+        mx = fmaxf(mx, fabsf(__ldg(&F[((size_t)m * ncol + col) * n_rho + i])));
+    }
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + col, __float_as_uint(mx));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// canonical K-major, no-swizzle offset of element (row, k) of a tile with 64 k
+__device__ __forceinline__ uint32_t tile_off(int row, int kgroup) {
+    return (uint32_t)((row >> 3) * 1024 + kgroup * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    const uint64_t lbo = 128, sbo = 1024;
+    return (uint64_t)((addr >> 4) & 0x3FFF) | (((lbo >> 4) & 0x3FFF) << 16) | (((sbo >> 4) & 0x3FFF) << 32) |
+           (1ull << 46);                      // version 1, base offset 0, no swizzle
+}
+
+__device__ __forceinline__ uint32_t instr_desc(int n, int fp16) {
+    const uint32_t ab = fp16 ? 0u : 1u;       // 0 = f16, 1 = bf16
+    return (1u << 4)                          // D = f32
+           | (ab << 7) | (ab << 10)           // A, B types
+           | ((uint32_t)(n >> 3) << 17)       // N >> 3
+           | ((uint32_t)(TC_M >> 4) << 24);   // M >> 4
+}
+
+__device__ __forceinline__ void split2(float x, int fp16, uint16_t* hi, uint16_t* lo) {
+    if (fp16) {
+        const __half h = __float2half_rn(x);
+        *hi = __half_as_ushort(h);
+        *lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        *hi = __bfloat16_as_ushort(h);
+        *lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, unsigned long long t_start) {
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+        if (done) return true;
+        if (global_ns() - t_start > TC_WAIT_NS) return false;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant__ TcParams p) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint8_t* fhi = sm;
+    uint8_t* flo = sm + TC_FTILE;
+    uint8_t* ahi = sm + 2 * TC_FTILE;
+    uint8_t* alo = ahi + p.ntmax * TC_KC * 2;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(alo + p.ntmax * TC_KC * 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+
+    const int m = blockIdx.x;
+    const int col0 = blockIdx.y * TC_M;
+    const int s = blockIdx.z;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Km = (p.n_max - m) / 2 + 1;
+    const int rowbase = p.mrow[m];
+    const int ib = s * p.chunk;
+    const int ie = min(p.n_rho, ib + p.chunk);
+    const int n_tiles = (Km + TC_NMAX - 1) / TC_NMAX;
+    const int nt_max = min(Km, TC_NMAX);
+    const int NTa = ((nt_max + 15) / 16) * 16;             // MMA N of the widest tile
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)NTa) ncols <<= 1;
+
+    const uint32_t bar_a = smem_u32(bar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_a), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const float* Fm = p.F + (size_t)m * p.ncol * p.n_rho;
+    const bool fvec = (p.n_rho & 3) == 0;
+    const bool avec = (p.n_rho & 7) == 0;
+    const unsigned long long t0 = global_ns();
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int nt = 0; nt < n_tiles && ok; ++nt) {
+        const int n0 = nt * TC_NMAX;
+        const int nrow = min(TC_NMAX, Km - n0);
+        const int NT = ((nrow + 15) / 16) * 16;
+        const uint32_t idesc = instr_desc(NT, p.fp16);
+        int first = 1;
+        for (int k0 = ib; k0 < ie && ok; k0 += TC_KC) {
+            // F chunk -> hi / lo tiles (128 rows x 64 k)
+            for (int task = tid; task < TC_M * 8; task += TC_THREADS) {
+                const int row = task >> 3, g = task & 7;
+                const int col = col0 + row;
+                const int kk = k0 + g * 8;
+                float x[8];
+                if (col < p.ncol) {
+                    const float* src = Fm + (size_t)col * p.n_rho + kk;
+                    if (fvec && kk + 8 <= ie) {
+                        const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+                        const float4 b = __ldg(reinterpret_cast<const float4*>(src) + 1);
+                        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+                        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] = (kk + e < ie) ? __ldg(src + e) : 0.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) x[e] = 0.f;
+                }
+                const float fs = (col < p.ncol) ? column_scale(p.colmax, col) : 1.f;
+                uint16_t h[8], l[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) split2(x[e] * fs, p.fp16, &h[e], &l[e]);
+                uint4 vh, vl;
+                vh.x = h[0] | ((uint32_t)h[1] << 16); vh.y = h[2] | ((uint32_t)h[3] << 16);
+                vh.z = h[4] | ((uint32_t)h[5] << 16); vh.w = h[6] | ((uint32_t)h[7] << 16);
+                vl.x = l[0] | ((uint32_t)l[1] << 16); vl.y = l[2] | ((uint32_t)l[3] << 16);
+                vl.z = l[4] | ((uint32_t)l[5] << 16); vl.w = l[6] | ((uint32_t)l[7] << 16);
+                const uint32_t o = tile_off(row, g);
+                *reinterpret_cast<uint4*>(fhi + o) = vh;
+                *reinterpret_cast<uint4*>(flo + o) = vl;
+            }
+            // A chunk (hi / lo, NT rows x 64 k)
+            for (int task = tid; task < NT * 8 * 2; task += TC_THREADS) {
+                const int half = task >= NT * 8;
+                const int t2 = half ? task - NT * 8 : task;
+                const int row = t2 >> 3, g = t2 & 7;
+                const int kk = k0 + g * 8;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (row < nrow) {
+                    const uint16_t* src = (half ? p.Alo : p.Ahi) + (size_t)(rowbase + n0 + row) * p.n_rho + kk;
+                    if (avec && kk + 8 <= ie) {
+                        v = __ldg(reinterpret_cast<const uint4*>(src));
+                    } else {
+                        uint16_t e8[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) e8[e] = (kk + e < ie) ? __ldg(src + e) : (uint16_t)0;
+                        v.x = e8[0] | ((uint32_t)e8[1] << 16); v.y = e8[2] | ((uint32_t)e8[3] << 16);
+                        v.z = e8[4] | ((uint32_t)e8[5] << 16); v.w = e8[6] | ((uint32_t)e8[7] << 16);
+                    }
+                }
+                *reinterpret_cast<uint4*>((half ? alo : ahi) + tile_off(row, g)) = v;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t fh = smem_u32(fhi), fl = smem_u32(flo), ah = smem_u32(ahi), al = smem_u32(alo);
+#pragma unroll
+                for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                    const uint32_t off = ks * 256;      // 16 k = two core matrices along K
+                    const uint64_t dfh = smem_desc(fh + off), dfl = smem_desc(fl + off);
+                    const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
+                    const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dfh), "l"(dah), "r"(idesc), "r"(acc0));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dfh), "l"(dal), "r"(idesc), "r"(1u));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dfl), "l"(dah), "r"(idesc), "r"(1u));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+                             : "memory");
+            }
+            first = 0;
+            // the tiles are rewritten next chunk: wait for the MMAs to finish reading them
+            bool done = mbar_wait(bar_a, phase, t0);
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            ok = __syncthreads_and(done) != 0;          // one decision for the whole CTA
+            if (!ok && tid == 0) atomicExch(p.status, ZM_ETIMEOUT);
+        }
+        if (!ok) break;
+        // epilogue: lanes 32w..32w+31 of TMEM = D rows (image columns)
+        const int col = col0 + warp * 32 + lane;
+        const float inv = (col < p.ncol) ? 1.0f / (p.a_scale * column_scale(p.colmax, col)) : 0.f;
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (col < p.ncol) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = c0 + j;
+                    if (n < nrow)
+                        p.part[((size_t)s * p.P + rowbase + n0 + n) * p.ncol + col] = __uint_as_float(r[j]) * inv;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (!ok) {
+        // a wait ran out: give in-flight MMAs a bounded time to drain before TMEM is freed
+        const unsigned long long t1 = global_ns();
+        mbar_wait(bar_a, phase ^ 1u, t1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    }
+}
+
+__global__ void k_project_reduce_tc(const float* __restrict__ part, int S, int P, int ncol,
+                                    const int2* __restrict__ pair_nm, const int* __restrict__ mrow, int batch,
+                                    int neumann, float* __restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= batch * P) return;
+    const int b = idx / P, q = idx - b * P;
+    const int2 nm = pair_nm[q];
+    const int row = mrow[nm.y] + (nm.x - nm.y) / 2;
+    float re = 0.f, im = 0.f;
+    for (int s = 0; s < S; ++s) {
+        const float* ps = part + ((size_t)s * P + row) * ncol + 2 * b;
+        re += ps[0];
+        im += ps[1];
+    }
+    const float f = (neumann && nm.y == 0) ? 0.5f : 1.f;
+    out[(size_t)idx * 2] = re * f;
+    out[(size_t)idx * 2 + 1] = im * f;
+}
+
+static int num_sms_tc(int dev) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    return n;
+}
+
 int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, cudaStream_t st) {
-    (void)p; (void)F; (void)batch; (void)out; (void)flags; (void)st;
-    return set_error(ZM_EUNSUPPORTED, "tensor-core projection is not built yet");
+    if (!p->Ahi || !p->Alo) return set_error(ZM_EINVAL, "plan has no tensor-core operands");
+    const int ncol = 2 * batch;
+    int s = ZM_OK;
+    const unsigned* colmax = nullptr;
+    if (p->prec == PREC_FP16X3) {
+        s = p->ws_colmax.grow(sizeof(unsigned) * (size_t)ncol);
+        if (s != ZM_OK) return s;
+        ZM_CUDA_TRY(cudaMemsetAsync(p->ws_colmax.ptr, 0, sizeof(unsigned) * (size_t)ncol, st));
+        k_colmax<<<dim3(ncol, 4), 256, 0, st>>>(F, p->n_max + 1, ncol, p->n_rho, (unsigned*)p->ws_colmax.ptr);
+        ZM_LAUNCH_CHECK("k_colmax");
+        colmax = (const unsigned*)p->ws_colmax.ptr;
+    }
+    const int ctiles = (ncol + TC_M - 1) / TC_M;
+    const int base = (p->n_max + 1) * ctiles;
+    const int target = 3 * num_sms_tc(p->device);
+    const int kchunks = (p->n_rho + TC_KC - 1) / TC_KC;
+    int S = std::max(1, std::min(kchunks, (target + base - 1) / base));
+    const int chunk = ((kchunks + S - 1) / S) * TC_KC;
+    S = (p->n_rho + chunk - 1) / chunk;
+    s = p->ws_part.grow(sizeof(float) * (size_t)S * p->P * ncol);
+    if (s != ZM_OK) return s;
+    TcParams tp;
+    tp.F = F;
+    tp.Ahi = p->Ahi;
+    tp.Alo = p->Alo;
+    tp.mrow = p->mrow;
+    tp.part = (float*)p->ws_part.ptr;
+    tp.status = p->status;
+    tp.n_max = p->n_max;
+    tp.n_rho = p->n_rho;
+    tp.ncol = ncol;
+    tp.P = p->P;
+    tp.chunk = chunk;
+    tp.fp16 = p->prec == PREC_FP16X3 ? 1 : 0;
+    tp.a_scale = p->a_scale;
+    tp.colmax = colmax;
+    // Shared memory also caps the resident CTAs so that their TMEM columns
+    // (<= 256 each) never exceed the SM's 512.
+    const int Km0 = p->n_max / 2 + 1;
+    const int NTa = ((std::min(Km0, TC_NMAX) + 15) / 16) * 16;
+    tp.ntmax = NTa;
+    int ncols = 32;
+    while (ncols < NTa) ncols <<= 1;
+    const size_t need = 2 * TC_FTILE + 2 * (size_t)NTa * TC_KC * 2 + 64;
+    const size_t cap = 227 * 1024;
+    const size_t by_tmem = cap / (512 / ncols) + 1024;
+    const size_t smem = std::max(need, std::min(cap, by_tmem));
+    static size_t configured[64] = {0};
+    int dev = p->device;
+    if (dev >= 64 || smem > configured[dev]) {
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev < 64) configured[dev] = smem;
+    }
+    dim3 grid(p->n_max + 1, ctiles, S);
+    k_project_tc<<<grid, TC_THREADS, smem, st>>>(tp);
+    ZM_LAUNCH_CHECK("k_project_tc");
+    const int tot = batch * p->P;
+    k_project_reduce_tc<<<(tot + 255) / 256, 256, 0, st>>>(tp.part, S, p->P, ncol, p->pair_nm, p->mrow, batch,
+                                                            (flags & ZM_NEUMANN) ? 1 : 0, out);
+    ZM_LAUNCH_CHECK("k_project_reduce_tc");
+    return ZM_OK;
 }
 
 }  // namespace zm

@@ -332,19 +332,30 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const __grid_constant__ 
     }
 }
 
-// mode 0/1: out[b] = (eps_1, eps, f_max, count) as doubles; mode 2: mm[b] = (min, max)
+// mode 0/1: out[b] = (eps_1, eps, f_max, count) as doubles; mode 2: mm[b] = (min, max).
+// One warp per image: lanes take two block records each, then a shuffle tree
+// (few dependent double additions).
 __global__ void k_reduce_final(const double* __restrict__ part, int batch, int mode, double* __restrict__ out,
                                float* __restrict__ mm) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= batch) return;
     double sd = 0, sf = 0, cnt = 0, mx = -INFINITY, mn = INFINITY;
-    for (int j = 0; j < RED_BLOCKS; ++j) {
+    for (int j = lane; j < RED_BLOCKS; j += 32) {
         const double* o = part + ((size_t)b * RED_BLOCKS + j) * 4;
         sd += o[0];
         if (mode == 2) mn = fmin(mn, o[1]); else sf += o[1];
         mx = fmax(mx, o[2]);
         cnt += o[3];
     }
+    for (int o = 16; o; o >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if (lane) return;
     if (mode == 2) {
         mm[2 * b] = (float)mn;
         mm[2 * b + 1] = (float)mx;
@@ -382,7 +393,7 @@ static int run_reduce(zm_plan_t p, int mode, const zm_image_t* ref, const zm_ima
         k_reduce<<<dim3(RED_BLOCKS, nb), RED_THREADS, 0, st>>>(rp);
         ZM_LAUNCH_CHECK("k_reduce");
     }
-    k_reduce_final<<<(batch + 127) / 128, 128, 0, st>>>((const double*)p->ws_red.ptr, batch, mode, out, mm);
+    k_reduce_final<<<(batch + 3) / 4, 128, 0, st>>>((const double*)p->ws_red.ptr, batch, mode, out, mm);
     ZM_LAUNCH_CHECK("k_reduce_final");
     return ZM_OK;
 }
@@ -460,9 +471,13 @@ static int check_canvases(const zm_canvas_t* cv, int batch) {
     return ZM_OK;
 }
 
+// moments are read, and polar rows written, as float2
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
 extern "C" int zm_reconstruct(zm_plan_t plan, const float* moments, int batch, float* out, unsigned flags,
                               void* stream) {
     if (!plan || !moments || !out) return set_error(ZM_EINVAL, "NULL argument");
+    if (!aligned8(moments) || !aligned8(out)) return set_error(ZM_EINVAL, "moments / out must be 8-byte aligned");
     if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
     if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
     DeviceGuard g(plan->device);
@@ -473,6 +488,8 @@ extern "C" int zm_reconstruct_cartesian(zm_plan_t plan, const float* moments, in
                                         const zm_canvas_t* canvases, float* polar_tmp, unsigned flags,
                                         void* stream) {
     if (!plan || !moments || !polar_tmp) return set_error(ZM_EINVAL, "NULL argument");
+    if (!aligned8(moments) || !aligned8(polar_tmp))
+        return set_error(ZM_EINVAL, "moments / polar_tmp must be 8-byte aligned");
     int s = check_canvases(canvases, batch);
     if (s != ZM_OK) return s;
     if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);

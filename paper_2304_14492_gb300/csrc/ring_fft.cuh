@@ -41,8 +41,11 @@ struct RingFFT {
     static constexpr int LOGQ = LOGM - LOGL;
     static constexpr int Q = 1 << LOGQ;              // points per lane
     // Row of M float2 with one float2 of padding per 16 (bank spread for the
-    // bit-reversed stores); in floats this is N + N/8.
-    static constexpr int ROW_FLOATS = N + N / 8;
+    // bit-reversed stores): N + N/8 floats, rounded up to a multiple of 4 so
+    // that every row starts 16-byte aligned.
+    static constexpr int ROW_FLOATS = ((N + N / 8 + 3) / 4) * 4;
+    static_assert(ROW_FLOATS % 4 == 0, "ring rows must stay 16-byte aligned");
+    static_assert(2 * (M + (M - 1) / 16) <= ROW_FLOATS, "padded spectrum must fit the row");
 
     __device__ static __forceinline__ int pad(int j) { return j + (j >> 4); }
     __device__ static __forceinline__ int brev_lane(int t) {

@@ -106,7 +106,9 @@ struct zm_plan_s {
     zm::Workspace ws_part;      // split-K partial sums of the projection
     zm::Workspace ws_G;         // reconstruction radial spectra G[b][m][2][n_rho]
     zm::Workspace ws_red;       // reduction partials
-    zm::Workspace ws_scale;     // per-image spectrum scale (fp16 split)
+    zm::Workspace ws_scale;     // per-image min / max (normalisation)
+    zm::Workspace ws_colmax;    // per-column max |F| (fp16 split scaling)
+    int* status = nullptr;      // device status word: ZM_ETIMEOUT after a timed-out wait
     // launch choices
     int kb_rings = 8;           // rings per CTA in the resample + FFT kernel
 };

@@ -53,6 +53,7 @@ SIGNATURES = {
     "zm_plan": (c_int, [POINTER(c_void_p), c_int, c_int, c_int, c_uint]),
     "zm_plan_destroy": (c_int, [c_void_p]),
     "zm_plan_reserve": (c_int, [c_void_p, c_int]),
+    "zm_plan_status": (c_int, [c_void_p]),
     "zm_plan_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
                              POINTER(c_uint)]),
     "zm_plan_table": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -181,6 +182,10 @@ def zm_plan_destroy(plan):
 
 def zm_plan_reserve(plan, batch):
     _check(lib().zm_plan_reserve(plan, batch))
+
+
+def zm_plan_status(plan):
+    _check(lib().zm_plan_status(plan))
 
 
 def zm_plan_info(plan):
