@@ -285,11 +285,11 @@ static int pick_rings(zm_plan_t p, int batch) {
     return R;
 }
 
-int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* F,
-                   float* fhat_out, bool resample_only, cudaStream_t st) {
+// Fused gather kernel on images [b0, b0 + nb) (any alignment): writes F and,
+// when fhat_out is set, the polar samples.
+static int launch_gather(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int batch, float* F, float* fhat_out,
+                         bool resample_only, cudaStream_t st) {
     const int R = pick_rings(p, batch);
-    p->kb_rings = R;
-    const int mode = fhat_in ? KB_POLAR : (resample_only ? KB_RESAMPLE : KB_GATHER);
     static thread_local KbParams kp;
     kp.n_rho = p->n_rho;
     kp.n_max = p->n_max;
@@ -299,17 +299,70 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
     kp.tw = p->tw;
     kp.F = F;
     kp.fhat_out = fhat_out;
-    kp.fhat_in = fhat_in;
-    for (int b0 = 0; b0 < batch; b0 += KB_MAX_IMG) {
-        const int nb = std::min(KB_MAX_IMG, batch - b0);
-        kp.b_off = b0;
-        if (imgs)
-            for (int j = 0; j < nb; ++j) kp.img[j] = resolve(imgs[b0 + j]);
-        int s;
-        if (mode == KB_POLAR) s = launch_kb_mode<KB_POLAR>(p->log_theta, kp, R, nb, st);
-        else if (mode == KB_RESAMPLE) s = launch_kb_mode<KB_RESAMPLE>(p->log_theta, kp, R, nb, st);
-        else s = launch_kb_mode<KB_GATHER>(p->log_theta, kp, R, nb, st);
+    kp.fhat_in = nullptr;
+    for (int c0 = b0; c0 < b0 + nb; c0 += KB_MAX_IMG) {
+        const int nc = std::min(KB_MAX_IMG, b0 + nb - c0);
+        kp.b_off = c0;
+        for (int j = 0; j < nc; ++j) kp.img[j] = resolve(imgs[c0 + j]);
+        const int s = resample_only ? launch_kb_mode<KB_RESAMPLE>(p->log_theta, kp, R, nc, st)
+                                    : launch_kb_mode<KB_GATHER>(p->log_theta, kp, R, nc, st);
         if (s != ZM_OK) return s;
+    }
+    return ZM_OK;
+}
+
+// Ring FFT of given polar samples fhat[b][i][k] -> F for images [b0, b0 + nb)
+// of a batch of `batch`.
+static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int batch, float* F, cudaStream_t st) {
+    const int R = pick_rings(p, batch);
+    static thread_local KbParams kp;
+    kp.n_rho = p->n_rho;
+    kp.n_max = p->n_max;
+    kp.batch_total = batch;
+    kp.rho32 = p->rho32;
+    kp.cs = p->cs;
+    kp.tw = p->tw;
+    kp.F = F;
+    kp.fhat_out = nullptr;
+    kp.fhat_in = fhat;
+    for (int c0 = b0; c0 < b0 + nb; c0 += 65535) {
+        const int nc = std::min(65535, b0 + nb - c0);
+        kp.b_off = c0;
+        const int s = launch_kb_mode<KB_POLAR>(p->log_theta, kp, R, nc, st);
+        if (s != ZM_OK) return s;
+    }
+    return ZM_OK;
+}
+
+// Ring spectra of a batch.  Polar input: FFT only.  Images: runs of
+// TMA-eligible images of one geometry go through the tile resampler into the
+// polar buffer (the caller's fhat_out, else the plan workspace) and then the
+// ring FFT; runs of other images take the fused gather kernel.
+int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* F,
+                   float* fhat_out, bool resample_only, cudaStream_t st) {
+    if (fhat_in) return launch_polar_fft(p, fhat_in, 0, batch, batch, F, st);
+    bool any_tma = false;
+    for (int b = 0; b < batch && !any_tma; ++b) any_tma = tma_eligible(imgs[b]);
+    float* fh = fhat_out;
+    if (any_tma && !fh) {
+        const int s = p->ws_fhat.grow(sizeof(float) * (size_t)batch * p->n_rho * p->n_theta);
+        if (s != ZM_OK) return s;
+        fh = (float*)p->ws_fhat.ptr;
+    }
+    int b = 0;
+    while (b < batch) {
+        int e = b + 1;
+        int s;
+        if (tma_eligible(imgs[b])) {
+            while (e < batch && tma_eligible(imgs[e]) && same_geometry(imgs[b], imgs[e])) ++e;
+            s = launch_resample_tiles(p, imgs, b, e - b, fh, st);
+            if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, st);
+        } else {
+            while (e < batch && !tma_eligible(imgs[e])) ++e;
+            s = launch_gather(p, imgs, b, e - b, batch, F, fhat_out, resample_only, st);
+        }
+        if (s != ZM_OK) return s;
+        b = e;
     }
     return ZM_OK;
 }

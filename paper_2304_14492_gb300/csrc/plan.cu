@@ -385,6 +385,7 @@ int build_plan_tables(zm_plan_t p) {
 
 static void free_plan(zm_plan_t p) {
     if (!p) return;
+    release_tiles(p);
     cudaFree(p->rho32);
     cudaFree(p->A32);
     cudaFree(p->R32m);

@@ -1,0 +1,322 @@
+// Bilinear polar resampling (Sec. 2.5) driven by Cartesian image tiles.
+//
+// Every polar sample (rho_i, theta_k) interpolates the 2x2 pixels whose top-left
+// corner ("anchor") is (floor X, floor Y).  The anchor plane is cut into 64x64
+// tiles; a work item is one tile plus the ring and angle ranges whose samples
+// can anchor in it (computed on the host from the geometry, with margins).
+// A CTA loads its tile and a one-pixel halo (a 68x65 box, zero outside the
+// image) with one TMA copy, evaluates the candidate samples, keeps those whose
+// anchor lies in the tile and writes them to f_hat[b][i][k].  Each image pixel
+// is read from HBM once and every gather is a shared-memory access; each
+// sample is claimed by exactly one tile because all tiles evaluate its
+// coordinates with the same float arithmetic.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "zm_internal.cuh"
+
+namespace zm {
+
+constexpr int TILE = 64;                 // anchors per tile side
+constexpr int BOX_W = TILE + 4;          // 16-byte multiple, covers x_t .. x_t + 64
+constexpr int BOX_H = TILE + 1;          // covers y_t .. y_t + 64
+constexpr int TILE_X0 = -4;              // x_t = -4 + 64 tx (multiple of 4, as TMA needs)
+constexpr int TILE_Y0 = -1;              // y_t = -1 + 64 ty
+constexpr int TILE_MAXC = 8192;          // candidates per work item
+constexpr int TILE_MAX_IMG = 64;         // tensor maps per launch
+constexpr int TILE_THREADS = 256;
+constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;
+
+struct TileItem {
+    int x_t, y_t;        // anchor origin of the tile
+    int i_lo, i_hi;      // rings [i_lo, i_hi)
+    int k_lo, k_n;       // angles (k_lo + j) mod N, j < k_n; k_lo in [0, N)
+};
+
+struct TileParams {
+    const TileItem* items;
+    const float* rho32;
+    const float2* cs;
+    float* fhat;
+    int* status;
+    int n_rho, N, b_off;
+    float cx, cy, r;
+    CUtensorMap maps[TILE_MAX_IMG];
+};
+
+__device__ __forceinline__ unsigned long long tile_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) k_resample_tiles(const __grid_constant__ TileParams p) {
+    __shared__ __align__(128) float tile[BOX_H * BOX_W];
+    __shared__ __align__(8) uint64_t bar;
+    const TileItem it = p.items[blockIdx.x];
+    const int bl = blockIdx.y;
+    const uint32_t bar_a = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+    const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(tile));
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        uint64_t pol;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"((uint32_t)(BOX_H * BOX_W * 4)) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+            " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst), "l"(&p.maps[bl]), "r"(it.x_t), "r"(it.y_t), "r"(bar_a),
+            "l"(pol)
+            : "memory");
+    }
+    __syncthreads();
+    const unsigned long long t0 = tile_ns();
+    bool done = false;
+    while (!done) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(ok) : "r"(bar_a) : "memory");
+        done = ok != 0;
+        if (!done && tile_ns() - t0 > TILE_WAIT_NS) break;
+    }
+    if (!__syncthreads_and(done)) {
+        // the copy did not arrive in time: report it, let it drain (bounded), leave
+        if (threadIdx.x == 0) {
+            atomicExch(p.status, ZM_ETIMEOUT);
+            const unsigned long long t1 = tile_ns();
+            uint32_t ok = 0;
+            while (!ok && tile_ns() - t1 < TILE_WAIT_NS)
+                asm volatile(
+                    "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
+                    : "=r"(ok) : "r"(bar_a) : "memory");
+        }
+        __syncthreads();
+        return;
+    }
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = p.N;
+    float* out = p.fhat + (size_t)(p.b_off + bl) * p.n_rho * N;
+    const float xt = (float)it.x_t, yt = (float)it.y_t;
+    for (int i = it.i_lo + warp; i < it.i_hi; i += TILE_THREADS / 32) {
+        const float rad = p.r * __ldg(&p.rho32[i]);
+        float* orow = out + (size_t)i * N;
+        for (int j = lane; j < it.k_n; j += 32) {
+            const int k = (it.k_lo + j) & (N - 1);
+            const float2 c = __ldg(&p.cs[k]);
+            const float X = fmaf(rad, c.x, p.cx);
+            const float Y = fmaf(-rad, c.y, p.cy);
+            const float xf = floorf(X), yf = floorf(Y);
+            const float lxf = xf - xt, lyf = yf - yt;
+            if (lxf >= 0.f && lxf < (float)TILE && lyf >= 0.f && lyf < (float)TILE) {
+                const int lx = (int)lxf, ly = (int)lyf;
+                const float fx = X - xf, fy = Y - yf;
+                const float* t0p = tile + ly * BOX_W + lx;
+                const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
+                const float top = fmaf(fx, p01 - p00, p00);
+                const float bot = fmaf(fx, p11 - p10, p10);
+                orow[k] = fmaf(fy, bot - top, top);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// An image can be staged by TMA when its base and row pitch are 16-byte
+// multiples and its extents fit the tensor-map limits.
+bool tma_eligible(const zm_image_t& im) {
+    return ((uintptr_t)im.data & 15u) == 0 && ((im.pitch * 4) & 15) == 0 && im.width <= (1 << 30) &&
+           im.height <= (1 << 30) && encode_fn() != nullptr;
+}
+
+static int encode_map(const zm_image_t& im, CUtensorMap* map) {
+    cuuint64_t dims[2] = {(cuuint64_t)im.width, (cuuint64_t)im.height};
+    cuuint64_t strides[1] = {(cuuint64_t)im.pitch * 4};
+    cuuint32_t box[2] = {BOX_W, BOX_H};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(im.data), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(ZM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ZM_OK;
+}
+
+struct TileList {
+    TileItem* items = nullptr;
+    int n = 0;
+    bool need_zero = false;   // some samples anchor outside every tile (they are 0)
+    ~TileList() { if (items) cudaFree(items); }
+};
+
+// Work items for one geometry.  Ring range from the distance range of the
+// tile's anchor rectangle to the centre (2 px margin); angle range from its
+// corners' polar angles (1.5 steps margin), the full circle when the centre is
+// within 2 px of the rectangle.
+static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
+    const int N = p->n_theta, n_rho = p->n_rho;
+    std::vector<double> rho(n_rho);
+    {
+        std::vector<float> r32(n_rho);
+        ZM_CUDA_TRY(cudaMemcpy(r32.data(), p->rho32, sizeof(float) * n_rho, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n_rho; ++i) rho[i] = (double)r32[i];
+    }
+    const double cx = g.cx, cy = g.cy, R = g.r;
+    const double rmax = R * rho[n_rho - 1];
+    const int ntx = (g.w + 3 - TILE_X0 + TILE - 1) / TILE;       // covers anchors up to w - 1
+    const int nty = (g.h + 0 - TILE_Y0 + TILE - 1) / TILE;       // covers anchors up to h - 1
+    const double gx0 = TILE_X0, gy0 = TILE_Y0, gx1 = TILE_X0 + (double)ntx * TILE, gy1 = TILE_Y0 + (double)nty * TILE;
+    // samples anchor within +-(rmax + float error) of the centre; those outside
+    // the tile grid see only zero pixels and are written by a memset
+    const double e = 0.5;
+    tl->need_zero = (cx - rmax - e < gx0) || (cx + rmax + e >= gx1) || (cy - rmax - e < gy0) || (cy + rmax + e >= gy1);
+    std::vector<std::pair<long, TileItem>> items;
+    const double kPi = 3.14159265358979323846, two_pi = 2.0 * kPi;
+    for (int ty = 0; ty < nty; ++ty) {
+        for (int tx = 0; tx < ntx; ++tx) {
+            const int x_t = TILE_X0 + tx * TILE, y_t = TILE_Y0 + ty * TILE;
+            // rectangle in centred coordinates, y up
+            const double u0 = x_t - cx, u1 = x_t + TILE - cx;
+            const double v0 = cy - (y_t + TILE), v1 = cy - y_t;
+            const double du = (u0 > 0) ? u0 : (u1 < 0 ? -u1 : 0.0);
+            const double dv = (v0 > 0) ? v0 : (v1 < 0 ? -v1 : 0.0);
+            const double dmin = std::sqrt(du * du + dv * dv);
+            const double mu = std::max(std::fabs(u0), std::fabs(u1)), mv = std::max(std::fabs(v0), std::fabs(v1));
+            const double dmax = std::sqrt(mu * mu + mv * mv);
+            if (dmin - 2.0 > rmax) continue;
+            const double lo = (dmin - 2.0) / R, hi = (dmax + 2.0) / R;
+            const int i_lo = (int)(std::lower_bound(rho.begin(), rho.end(), lo) - rho.begin());
+            const int i_hi = (int)(std::upper_bound(rho.begin(), rho.end(), hi) - rho.begin());
+            if (i_lo >= i_hi) continue;
+            int k_lo = 0, k_n = N;
+            if (dmin > 2.0) {
+                const double ac = std::atan2(0.5 * (v0 + v1), 0.5 * (u0 + u1));
+                double dlo = 0, dhi = 0;
+                const double us[2] = {u0, u1}, vs[2] = {v0, v1};
+                for (double uu : us)
+                    for (double vv : vs) {
+                        double d = std::atan2(vv, uu) - ac;
+                        while (d > kPi) d -= two_pi;
+                        while (d <= -kPi) d += two_pi;
+                        dlo = std::min(dlo, d);
+                        dhi = std::max(dhi, d);
+                    }
+                const double ka = (ac + dlo) * N / two_pi - 1.5, kb = (ac + dhi) * N / two_pi + 1.5;
+                const long kl = (long)std::floor(ka), kh = (long)std::ceil(kb);
+                if (kh - kl + 1 < N) {
+                    k_lo = (int)(((kl % N) + N) % N);
+                    k_n = (int)(kh - kl + 1);
+                }
+            }
+            // split heavy tiles by ring ranges
+            const int per = std::max(1, TILE_MAXC / k_n);
+            for (int a = i_lo; a < i_hi; a += per) {
+                TileItem t{x_t, y_t, a, std::min(i_hi, a + per), k_lo, k_n};
+                items.push_back({(long)(t.i_hi - t.i_lo) * k_n, t});
+            }
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<TileItem> h(items.size());
+    for (size_t j = 0; j < items.size(); ++j) h[j] = items[j].second;
+    tl->n = (int)h.size();
+    if (tl->n) {
+        ZM_CUDA_TRY(cudaMalloc(&tl->items, sizeof(TileItem) * h.size()));
+        ZM_CUDA_TRY(cudaMemcpy(tl->items, h.data(), sizeof(TileItem) * h.size(), cudaMemcpyHostToDevice));
+    }
+    return ZM_OK;
+}
+
+// Work lists cached per (plan, geometry); released with the plan.
+struct TileCache {
+    std::mutex mu;
+    std::map<std::tuple<zm_plan_t, int, int, float, float, float>, std::unique_ptr<TileList>> lists;
+};
+static TileCache g_tiles;
+
+void release_tiles(zm_plan_t p) {
+    std::lock_guard<std::mutex> lk(g_tiles.mu);
+    for (auto it = g_tiles.lists.begin(); it != g_tiles.lists.end();) {
+        if (std::get<0>(it->first) == p) it = g_tiles.lists.erase(it);
+        else ++it;
+    }
+}
+
+static int get_tiles(zm_plan_t p, const GeoImage& g, TileList** out) {
+    std::lock_guard<std::mutex> lk(g_tiles.mu);
+    auto key = std::make_tuple(p, g.h, g.w, g.cx, g.cy, g.r);
+    auto it = g_tiles.lists.find(key);
+    if (it == g_tiles.lists.end()) {
+        auto tl = std::make_unique<TileList>();
+        const int s = build_tiles(p, g, tl.get());
+        if (s != ZM_OK) return s;
+        it = g_tiles.lists.emplace(key, std::move(tl)).first;
+    }
+    *out = it->second.get();
+    return ZM_OK;
+}
+
+// Resample images [b0, b0 + nb) (all TMA-eligible, one geometry) into
+// fhat[b][i][k] (fhat points at image 0 of the whole batch).
+int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st) {
+    const GeoImage g = resolve(imgs[b0]);
+    TileList* tl = nullptr;
+    int s = get_tiles(p, g, &tl);
+    if (s != ZM_OK) return s;
+    const size_t per_img = (size_t)p->n_rho * p->n_theta;
+    if (tl->need_zero) ZM_CUDA_TRY(cudaMemsetAsync(fhat + (size_t)b0 * per_img, 0, sizeof(float) * per_img * nb, st));
+    if (tl->n == 0) return ZM_OK;
+    static thread_local TileParams tp;
+    tp.items = tl->items;
+    tp.rho32 = p->rho32;
+    tp.cs = p->cs;
+    tp.fhat = fhat;
+    tp.status = p->status;
+    tp.n_rho = p->n_rho;
+    tp.N = p->n_theta;
+    tp.cx = g.cx;
+    tp.cy = g.cy;
+    tp.r = g.r;
+    for (int c0 = 0; c0 < nb; c0 += TILE_MAX_IMG) {
+        const int nc = std::min(TILE_MAX_IMG, nb - c0);
+        tp.b_off = b0 + c0;
+        for (int j = 0; j < nc; ++j) {
+            s = encode_map(imgs[b0 + c0 + j], &tp.maps[j]);
+            if (s != ZM_OK) return s;
+        }
+        k_resample_tiles<<<dim3(tl->n, nc), TILE_THREADS, 0, st>>>(tp);
+        ZM_LAUNCH_CHECK("k_resample_tiles");
+    }
+    return ZM_OK;
+}
+
+bool same_geometry(const zm_image_t& a, const zm_image_t& b) {
+    const GeoImage ga = resolve(a), gb = resolve(b);
+    return ga.h == gb.h && ga.w == gb.w && ga.cx == gb.cx && ga.cy == gb.cy && ga.r == gb.r;
+}
+
+}  // namespace zm

@@ -103,6 +103,7 @@ struct zm_plan_s {
     std::vector<int> mrow_h;
     // workspace (grown on demand)
     zm::Workspace ws_F;         // ring spectra F[m][b][2][n_rho] (fp32)
+    zm::Workspace ws_fhat;      // polar samples f[b][i][k] (fp32)
     zm::Workspace ws_part;      // split-K partial sums of the projection
     zm::Workspace ws_G;         // reconstruction radial spectra G[b][m][2][n_rho]
     zm::Workspace ws_red;       // reduction partials
@@ -159,5 +160,11 @@ inline GeoImage resolve(const zm_image_t& im) {
 }
 
 int check_images(const zm_image_t* imgs, int batch);
+
+// Cartesian-tile resampling (resample_tiles.cu)
+bool tma_eligible(const zm_image_t& im);
+bool same_geometry(const zm_image_t& a, const zm_image_t& b);
+int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st);
+void release_tiles(zm_plan_t p);
 
 }  // namespace zm

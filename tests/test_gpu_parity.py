@@ -95,30 +95,52 @@ def test_table_eq7_matches_recurrence(n_max, n_rho, n_theta, flags):
 
 
 # ------------------------------------------------------------------ a2: resampling
+def gpu_resample(plan_args, imgs, geometries=None, views=None):
+    n_max, n_rho, n_theta = plan_args
+    with Plan(n_max, n_rho, n_theta) as p:
+        f = torch.full((len(imgs), n_rho, n_theta), float("nan"), device=DEV)
+        ts = views if views is not None else [dev(i) for i in imgs]
+        zm.zm_resample(p.h, ts, f, geometries=geometries)
+        torch.cuda.synchronize()
+    return f.double().cpu().numpy()
+
+
 @pytest.mark.parametrize("shape,n_rho,n_theta,geometry", [
-    ((64, 64), 32, 64, None), ((45, 70), 21, 32, None), ((50, 40), 17, 64, (10.25, 30.5, 28.0))])
+    ((64, 64), 32, 64, None), ((45, 70), 21, 32, None), ((50, 40), 17, 64, (10.25, 30.5, 28.0)),
+    ((40, 36), 25, 128, (18.0, 20.0, 60.0)),          # disk larger than the image
+    ((300, 200), 100, 512, (60.5, 250.0, 55.0)),      # off-centre disk
+    ((8, 8), 3, 8, None), ((1, 1), 2, 8, None)])
 def test_resample_matches_oracle(shape, n_rho, n_theta, geometry):
     img = synth.uniform_image(*shape, workload=11, index=0)
-    with Plan(4, n_rho, n_theta) as p:
-        f = torch.empty((1, n_rho, n_theta), device=DEV)
-        zm.zm_resample(p.h, [dev(img)], f, geometries=[geometry] if geometry else None)
-        torch.cuda.synchronize()
+    got = gpu_resample((4 if n_theta >= 16 else 3, n_rho, n_theta), [img], [geometry] if geometry else None)[0]
     rho, _ = grid.radial_nodes(n_rho)
     ref = resample.polar_resample(img.astype(np.float64), rho, n_theta, geometry)
-    assert np.max(np.abs(f[0].double().cpu().numpy() - ref)) <= 2e-5
+    assert not np.isnan(got).any()
+    assert np.max(np.abs(got - ref)) <= 2e-5
 
 
-def test_resample_strided_rows():
+def test_resample_4k_frame():
+    img = synth.blob_image(2160, 3840, 32, workload=2, index=0)
+    got = gpu_resample((100, 1024, 1024), [img])[0]
+    rho, _ = grid.radial_nodes(1024)
+    ref = resample.polar_resample(img.astype(np.float64), rho, 1024)
+    assert not np.isnan(got).any()
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def test_resample_strided_and_unaligned_views():
+    # a pitch-100 view (16-byte aligned rows: tile path) and a view shifted by one
+    # column (unaligned base: fused gather path) in one batch
     big = synth.uniform_image(80, 100, workload=12, index=0)
-    t = dev(big)[5:69, 10:74]                          # 64 x 64 view, pitch 100
-    img = big[5:69, 10:74]
-    with Plan(4, 32, 64) as p:
-        f = torch.empty((1, 32, 64), device=DEV)
-        zm.zm_resample(p.h, [t], f)
-        torch.cuda.synchronize()
+    t = dev(big)
+    views = [t[4:68, 8:72], t[5:69, 9:73], t[4:68, 8:72]]
+    imgs = [big[4:68, 8:72], big[5:69, 9:73], big[4:68, 8:72]]
+    got = gpu_resample((4, 32, 64), imgs, views=views)
     rho, _ = grid.radial_nodes(32)
-    ref = resample.polar_resample(img.astype(np.float64), rho, 64)
-    assert np.max(np.abs(f[0].double().cpu().numpy() - ref)) <= 2e-5
+    for b in range(3):
+        ref = resample.polar_resample(imgs[b].astype(np.float64), rho, 64)
+        assert not np.isnan(got[b]).any()
+        assert np.max(np.abs(got[b] - ref)) <= 2e-5
 
 
 # ------------------------------------------------------------------ a3: ring spectra
@@ -205,6 +227,20 @@ def test_moments_ragged_and_uneven():
         Z = gpu_moments(p, imgs, geometries=[g if g else (0, 0, -1) for g in geos])
         for b in range(3):
             assert metrics.rel_max_err(Z[b], oracle_moments(imgs[b], p, geometry=geos[b])) <= TOL_Z
+
+
+def test_moments_mixed_alignment_batch():
+    big = synth.blob_image(140, 150, 6, workload=14, index=0)
+    t = dev(big)
+    views = [t[0:128, 0:128], t[1:129, 3:131], t[6:134, 8:136]]
+    imgs = [big[0:128, 0:128], big[1:129, 3:131], big[6:134, 8:136]]
+    with Plan(30, 64, 64) as p:
+        out = torch.empty((3, p.P, 2), device=DEV)
+        zm.zm_moments(p.h, views, out)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+        for b in range(3):
+            assert metrics.rel_max_err(Z[b], oracle_moments(imgs[b], p)) <= TOL_Z
 
 
 def test_moments_batch_spanning_launches_and_order_independence():
