@@ -6,8 +6,8 @@ Workload: 3840x2160 float32 frames of 32 random anisotropic Gaussian blobs
 of standard deviation 0.01, the disk of diameter 2160 centred; moments up to
 n_max = 100 on a 1024 x 1024 polar grid.  A step is one pass of the whole hot
 path over a batch of B frames already resident in HBM:
-  ring spectra (bilinear polar resampling + ring real FFT, polar samples kept)
-  -> radial projection (Eq. 1) -> reconstruction on the polar nodes (Eq. 9,
+  bilinear polar resampling (Sec. 2.5, polar samples kept) -> ring real FFT
+  and radial projection (Eq. 1) -> reconstruction on the polar nodes (Eq. 9,
   Neumann) -> reconstruction errors on the polar nodes (Eq. 10, Eq. 13).
 The FP64 radial-polynomial table (Eq. 7) is built once at plan time, outside
 the timed region, and reported as plan_ms.
@@ -144,8 +144,8 @@ def read_profile_traffic(kernel_tag):
     """Per-launch DRAM bytes of `kernel_tag` from the committed ncu summary, if
     the summary was taken on the current kernel source."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_ring_spectra_4k.md")
-    src = os.path.join(ROOT, "paper_2304_14492_gb300", "csrc", "moments.cu")
+    path = os.path.join(ROOT, "profiles", kernel_tag + "_4k.md")
+    src = os.path.join(ROOT, "paper_2304_14492_gb300", "csrc", "resample_tiles.cu")
     if not (os.path.exists(path) and os.path.exists(src)):
         return None, None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
@@ -280,21 +280,27 @@ def run_gb300(args):
     zm.zm_plan_reserve(plan32, B)
 
     st = torch.cuda.current_stream(dev)
-    spectra = torch.empty((N_MAX + 1, B, 2, N_RHO), device=dev)
     out = torch.empty((B, P, 2), device=dev)
     fhat = torch.empty((B, N_RHO, N_THETA), device=dev)
     frec = torch.empty((B, N_RHO, N_THETA), device=dev)
     err = torch.empty((B, 4), device=dev, dtype=torch.float64)
 
-    def step(kb_events=None):
-        if kb_events is not None:
-            kb_events[0].record(st)
-        zm.zm_ring_spectra(plan, views, spectra, fhat, st)
-        if kb_events is not None:
-            kb_events[1].record(st)
-        zm.zm_project(plan, spectra, B, out, 0, st)
+    def step(ev=None):
+        # resampling (tile kernel) | ring FFT + projection | reconstruction | errors
+        if ev is not None:
+            ev[0].record(st)
+        zm.zm_resample(plan, views, fhat, st)
+        if ev is not None:
+            ev[1].record(st)
+        zm.zm_moments_polar(plan, fhat, B, out, 0, st)
+        if ev is not None:
+            ev[2].record(st)
         zm.zm_reconstruct(plan, out, B, frec, zm.ZM_NEUMANN, st)
+        if ev is not None:
+            ev[3].record(st)
         zm.zm_errors_polar(plan, fhat, frec, B, err, st)
+        if ev is not None:
+            ev[4].record(st)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -309,7 +315,7 @@ def run_gb300(args):
         gpu_id = str(local)
     sampler = ClockSampler(gpu_id)
     sampler.start()
-    kb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kb = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     l0 = zm.zm_launch_count()
@@ -325,14 +331,16 @@ def run_gb300(args):
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    kb_ms = statistics.mean(a.elapsed_time(b) for a, b in kb)
+    seg = [statistics.mean(e[j].elapsed_time(e[j + 1]) for e in kb) for j in range(4)]
+    kb_ms = seg[0]
     value = world * B * args.steps / (ms / 1000.0)
 
-    # roofline of the dominant kernel (ring spectra): algorithmic bytes per launch
+    # roofline of the dominant kernel (tile resampler): algorithmic bytes per
+    # launch = touched image sectors + polar samples written, per frame
     sectors = touched_sector_bytes()
     f_bytes = (N_MAX + 1) * N_RHO * 8
     fhat_bytes = N_RHO * N_THETA * 4
-    kb_bytes = B * (sectors + f_bytes + fhat_bytes)
+    kb_bytes = B * (sectors + fhat_bytes)
     import json as _json
     peaks = {}
     try:
@@ -341,13 +349,15 @@ def run_gb300(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = kb_bytes / (kb_ms / 1000.0) / 1e9
-    traffic, traffic_note = read_profile_traffic("k_ring_spectra")
-    roofline = {"bound": "hbm", "kernel": "k_ring_spectra", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+    traffic, traffic_note = read_profile_traffic("k_resample_tiles")
+    roofline = {"bound": "hbm", "kernel": "k_resample_tiles", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": (traffic * B if traffic else None),
                 "algorithmic_bytes_per_launch": kb_bytes, "launch_ms": kb_ms,
                 "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback",
-                "per_image_bytes": {"touched_sectors": sectors, "spectra_out": f_bytes, "polar_samples_out": fhat_bytes,
-                                    "disk_box": disk_box_bytes()}}
+                "per_image_bytes": {"touched_sectors": sectors, "polar_samples_out": fhat_bytes,
+                                    "disk_box": disk_box_bytes()},
+                "step_segments_ms": {"resample": seg[0], "ring_fft+projection": seg[1], "reconstruction": seg[2],
+                                     "errors": seg[3]}}
     if traffic_note:
         roofline["traffic_note"] = traffic_note
 
@@ -358,7 +368,7 @@ def run_gb300(args):
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "global_batch": B * world,
                        "precision": prec, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (%d MB of frames per step)" % (B * H * W * 4 // 2**20),
-                       "step": "ring spectra + projection + polar reconstruction (Neumann) + polar errors"},
+                       "step": "resampling + ring FFT + projection + polar reconstruction (Neumann) + polar errors"},
             "roofline": roofline, "gpu_launches": l1 - l0, "clocks": clocks, "plan_ms": plan_ms}
 
     if rank == 0 and not args.quick:
