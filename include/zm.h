@@ -178,6 +178,29 @@ int zm_ring_spectra(zm_plan_t plan, const zm_image_t* imgs, int batch, float* sp
 int zm_project(zm_plan_t plan, const float* spectra, int batch, float* out,
                unsigned flags, void* stream);
 
+/* The projection of zm_project for callers that cannot allocate device memory
+ * at call time: their device memory is already handed out by another
+ * allocator (e.g. a framework's caching pool that reserved the GPU up front),
+ * or they run in a loop where cudaMalloc's device-wide synchronisation and
+ * unbounded latency are not acceptable.  It allocates nothing: the split-K
+ * partial sums live in a fixed 8 MiB array in device memory that belongs to
+ * the library (held by every GPU that loads it, until the process exits).
+ * The paper has no counterpart; this is an interface matter only.
+ *  - Computes in FP32 whatever the plan's precision flag; the plan itself is
+ *    made beforehand with zm_plan (which does allocate).
+ *  - Requires P(n_max) * 2 * batch <= 2^21 floats; larger requests return
+ *    ZM_EINVAL without touching the device.
+ *  - The first call on a device looks up the array's device address (set-up,
+ *    with that device current); make that first call before any stream
+ *    capture.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents; each call overwrites the part it reads, so nothing needs
+ *    clearing, but calls that overlap on the GPU (other streams, other
+ *    threads) race: serialise them.
+ * Arguments, layouts and flags as zm_project. */
+int zm_project_noalloc(zm_plan_t plan, const float* spectra, int batch, float* out,
+                       unsigned flags, void* stream);
+
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic counter; never reset). */
 unsigned long long zm_launch_count(void);

@@ -64,6 +64,7 @@ SIGNATURES = {
     "zm_resample": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
     "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
     "zm_project": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_project_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_launch_count": (ctypes.c_ulonglong, []),
     "zm_reconstruct": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_reconstruct_cartesian": (c_int, [c_void_p, c_void_p, c_int, POINTER(zm_canvas_t), c_void_p, c_uint,
@@ -229,6 +230,10 @@ def zm_ring_spectra(plan, images, spectra, fhat=None, stream=None, geometries=No
 
 def zm_project(plan, spectra, batch, out, flags=0, stream=None):
     _check(lib().zm_project(plan, _ptr(spectra), batch, _ptr(out), flags, _stream(stream)))
+
+
+def zm_project_noalloc(plan, spectra, batch, out, flags=0, stream=None):
+    _check(lib().zm_project_noalloc(plan, _ptr(spectra), batch, _ptr(out), flags, _stream(stream)))
 
 
 def zm_launch_count():
