@@ -220,6 +220,16 @@ int zm_reconstruct(zm_plan_t plan, const float* moments, int batch, float* out,
                    unsigned flags, void* stream);
 
 /*
+ * zm_reconstruct fused with zm_errors_polar: the polar reconstruction is
+ * compared, inside the same kernel, with the polar samples `fhat` (device
+ * float[batch][N_rho][N_theta], e.g. kept by zm_moments_ex) and err (device
+ * double[batch][4]) receives eps_1 (Eq. 10), eps (Eq. 13), f_max and the node
+ * count.  `out` receives the reconstruction, or may be NULL.
+ */
+int zm_reconstruct_errors(zm_plan_t plan, const float* moments, int batch, float* out,
+                          const float* fhat, double* err, unsigned flags, void* stream);
+
+/*
  * Reconstruction onto pixels: the polar reconstruction above, then bilinear
  * interpolation in (ring, angle) at every pixel centre of each canvas inside
  * its disk (ring bracket rho_i <= rho < rho_{i+1}, clamped to the first / last

@@ -76,10 +76,21 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
     float* rings = smem;
 
     if (MODE == KB_POLAR) {
-        for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-            const int r = idx >> LOGN, k = idx & (N - 1);
-            const int i = i0 + r;
-            rings[r * ROW + k] = (i < n_rho) ? __ldg(&p.fhat_in[((size_t)b * n_rho + i) * N + k]) : 0.f;
+        if (LOGN >= 2 && (reinterpret_cast<uintptr_t>(p.fhat_in) & 15) == 0) {
+            constexpr int LOGN4 = LOGN >= 2 ? LOGN - 2 : 0;
+            for (int idx = threadIdx.x; idx < (R * N) >> 2; idx += blockDim.x) {
+                const int r = idx >> LOGN4, k4 = idx & ((N >> 2) - 1);
+                const int i = i0 + r;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < n_rho) v = __ldg(reinterpret_cast<const float4*>(p.fhat_in + ((size_t)b * n_rho + i) * N) + k4);
+                *reinterpret_cast<float4*>(rings + r * ROW + 4 * k4) = v;
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+                const int r = idx >> LOGN, k = idx & (N - 1);
+                const int i = i0 + r;
+                rings[r * ROW + k] = (i < n_rho) ? __ldg(&p.fhat_in[((size_t)b * n_rho + i) * N + k]) : 0.f;
+            }
         }
     } else {
         const GeoImage im = p.img[bl];
@@ -129,12 +140,14 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
         }
     }
     __syncthreads();
-    const int tot = 2 * (n_max + 1) * R;
+    const int lgR = __ffs(R) - 1;                 // R is a power of two
+    const int nm1 = n_max + 1;
+    const int tot = 2 * nm1 * R;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int r = e % R;
-        const int cm = e / R;
-        const int c = cm / (n_max + 1);
-        const int m = cm - c * (n_max + 1);
+        const int r = e & (R - 1);
+        const int cm = e >> lgR;
+        const int c = cm >= nm1 ? 1 : 0;
+        const int m = cm - c * nm1;
         const int i = i0 + r;
         if (i < n_rho) p.F[(((size_t)m * p.batch_total + b) * 2 + c) * n_rho + i] = Fs[e];
     }

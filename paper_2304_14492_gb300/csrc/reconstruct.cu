@@ -15,28 +15,48 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 // ============================================================== radial part
 // G[b][m][re/im][i] = c_m sum_{n = m, m+2, ..} R_nm(rho_i) Z_nm, with
 // c_m = 2/eps_m (c_0 = 1, c_m = 2) for the literal Eq. 9 and c_m = 1 for the
-// half sum over the stored m >= 0.
+// half sum over the stored m >= 0.  One thread = one node i, one m and RB
+// images (their moments staged in shared memory), so each table value is
+// read once per RB images.
+constexpr int RB = 8;
+
 __global__ void __launch_bounds__(128)
 k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, const int* __restrict__ mrow,
-               int n_max, int n_rho, int P, int neumann, float* __restrict__ G) {
+               int n_max, int n_rho, int P, int batch, int neumann, float* __restrict__ G) {
+    extern __shared__ float2 zs[];                 // [RB][Km]
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = blockIdx.y;
-    const int b = blockIdx.z;
-    if (i >= n_rho) return;
+    const int b0 = blockIdx.z * RB;
+    const int nb = min(RB, batch - b0);
     const int Km = (n_max - m) / 2 + 1;
     const int row0 = mrow[m];
-    const float2* Zb = Z + (size_t)b * P;
-    float re = 0.f, im = 0.f;
+    for (int t = threadIdx.x; t < RB * Km; t += blockDim.x) {
+        const int bb = t / Km, j = t - bb * Km;
+        zs[t] = (bb < nb) ? __ldg(&Z[(size_t)(b0 + bb) * P + moment_index(m + 2 * j, m)]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (i >= n_rho) return;
+    float re[RB], im[RB];
+#pragma unroll
+    for (int bb = 0; bb < RB; ++bb) re[bb] = im[bb] = 0.f;
     for (int j = 0; j < Km; ++j) {
         const float r = __ldg(&R32m[(size_t)(row0 + j) * n_rho + i]);
-        const float2 z = __ldg(&Zb[moment_index(m + 2 * j, m)]);
-        re = fmaf(r, z.x, re);
-        im = fmaf(r, z.y, im);
+#pragma unroll
+        for (int bb = 0; bb < RB; ++bb) {
+            const float2 z = zs[bb * Km + j];
+            re[bb] = fmaf(r, z.x, re[bb]);
+            im[bb] = fmaf(r, z.y, im[bb]);
+        }
     }
     const float c = (neumann && m > 0) ? 2.f : 1.f;
-    float* g = G + (((size_t)b * (n_max + 1) + m) * 2) * n_rho + i;
-    g[0] = c * re;
-    g[n_rho] = c * im;
+#pragma unroll
+    for (int bb = 0; bb < RB; ++bb) {
+        if (bb < nb) {
+            float* g = G + (((size_t)(b0 + bb) * (n_max + 1) + m) * 2) * n_rho + i;
+            g[0] = c * re[bb];
+            g[n_rho] = c * im[bb];
+        }
+    }
 }
 
 // ============================================================== ring inverse FFT
@@ -46,10 +66,14 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // is the M-point inverse DFT of
 //   C_m = (S_m + conj S_{M-m}) + i e^{2 pi i m/N} (S_m - conj S_{M-m}),
 // computed as conj(DFT(conj C)) by the same warp FFT as the forward path.
-template <int LOGN>
+// With ERR, the CTA also accumulates, against the reference polar samples
+// `ref`, sum (ref - f~)^2, sum ref^2, max ref and the node count over its rings
+// into one record part[b][blockIdx.x] (Eq. 10 / Eq. 13 on the polar nodes); `out`
+// may then be NULL.
+template <int LOGN, bool ERR>
 __global__ void __launch_bounds__(512)
 k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho,
-             float* __restrict__ out) {
+             float* __restrict__ out, const float* __restrict__ ref, double* __restrict__ part) {
     using FFT = RingFFT<LOGN>;
     constexpr int N = FFT::N;
     constexpr int M = FFT::M;
@@ -96,15 +120,61 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     }
     __syncwarp();
     const int i = i0 + warp;
+    float sd = 0.f, sf = 0.f, mx = -INFINITY, cnt = 0.f;
     if (i < n_rho) {
-        float2* o = reinterpret_cast<float2*>(out + ((size_t)b * n_rho + i) * N);
-        for (int j = lane; j < M; j += 32) o[j] = X[FFT::pad(j)];
+        const size_t row = ((size_t)b * n_rho + i) * N;
+        float2* o = out ? reinterpret_cast<float2*>(out + row) : nullptr;
+        const float2* rf = ERR ? reinterpret_cast<const float2*>(ref + row) : nullptr;
+        for (int j = lane; j < M; j += 32) {
+            const float2 x = X[FFT::pad(j)];
+            if (o) o[j] = x;
+            if (ERR) {
+                const float2 f = __ldg(&rf[j]);
+                const float d0 = f.x - x.x, d1 = f.y - x.y;
+                sd = fmaf(d0, d0, fmaf(d1, d1, sd));
+                sf = fmaf(f.x, f.x, fmaf(f.y, f.y, sf));
+                mx = fmaxf(mx, fmaxf(f.x, f.y));
+                cnt += 2.f;
+            }
+        }
+    }
+    if (ERR) {
+        for (int o2 = 16; o2; o2 >>= 1) {
+            sd += __shfl_xor_sync(0xffffffffu, sd, o2);
+            sf += __shfl_xor_sync(0xffffffffu, sf, o2);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
+        }
+        __syncthreads();                                  // the rows are free again: reuse as scratch
+        float* red = smem;
+        if (lane == 0) {
+            red[4 * warp + 0] = sd;
+            red[4 * warp + 1] = sf;
+            red[4 * warp + 2] = mx;
+            red[4 * warp + 3] = cnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, c = 0, n = 0;
+            float m = -INFINITY;
+            for (int w = 0; w < R; ++w) {
+                a += red[4 * w];
+                c += red[4 * w + 1];
+                m = fmaxf(m, red[4 * w + 2]);
+                n += red[4 * w + 3];
+            }
+            double* o = part + ((size_t)b * gridDim.x + blockIdx.x) * 4;
+            o[0] = a;
+            o[1] = c;
+            o[2] = (double)m;
+            o[3] = n;
+        }
     }
 }
 
-template <int LOGN>
+template <int LOGN, bool ERR>
 static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho, int batch, float* out,
-                         cudaStream_t st) {
+                         const float* ref, double* part, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const int R = 8;
     const size_t smem = sizeof(float) * (size_t)R * FFT::ROW_FLOATS + sizeof(float2) * (size_t)R * (n_max + 1);
@@ -112,40 +182,84 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
     cudaGetDevice(&dev);
     static size_t configured[64] = {0};
     if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
-        ZM_CUDA_TRY(cudaFuncSetAttribute(k_recon_ifft<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_recon_ifft<LOGN, ERR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
         if (dev < 64) configured[dev] = smem;
     }
     dim3 grid((n_rho + R - 1) / R, batch);
-    k_recon_ifft<LOGN><<<grid, R * 32, smem, st>>>(G, tw, n_max, n_rho, out);
+    k_recon_ifft<LOGN, ERR><<<grid, R * 32, smem, st>>>(G, tw, n_max, n_rho, out, ref, part);
     ZM_LAUNCH_CHECK("k_recon_ifft");
+    return ZM_OK;
+}
+
+template <bool ERR>
+static int launch_ifft(zm_plan_t p, const float* G, int batch, float* out, const float* ref, double* part,
+                       cudaStream_t st) {
+    switch (p->log_theta) {
+        case 3: return launch_ifft_t<3, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 4: return launch_ifft_t<4, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 5: return launch_ifft_t<5, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 6: return launch_ifft_t<6, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 7: return launch_ifft_t<7, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 8: return launch_ifft_t<8, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 9: return launch_ifft_t<9, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 10: return launch_ifft_t<10, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 11: return launch_ifft_t<11, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", p->log_theta);
+    }
+}
+
+static int launch_radial(zm_plan_t p, const float* moments, int batch, unsigned flags, cudaStream_t st,
+                         float** G_out) {
+    const int s = p->ws_G.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
+    if (s != ZM_OK) return s;
+    float* G = (float*)p->ws_G.ptr;
+    const size_t smem = sizeof(float2) * RB * (size_t)(p->n_max / 2 + 1);
+    int dev = p->device;
+    static size_t configured[64] = {0};
+    if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_recon_radial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev < 64) configured[dev] = smem;
+    }
+    const int nz = (batch + RB - 1) / RB;
+    for (int z0 = 0; z0 < nz; z0 += 65535) {
+        const int nzc = std::min(65535, nz - z0);
+        const int b0 = z0 * RB;
+        const int nbc = std::min(batch - b0, nzc * RB);
+        dim3 grid((p->n_rho + 127) / 128, p->n_max + 1, nzc);
+        k_recon_radial<<<grid, 128, smem, st>>>(p->R32m, (const float2*)moments + (size_t)b0 * p->P, p->mrow,
+                                                 p->n_max, p->n_rho, p->P, nbc, (flags & ZM_NEUMANN) ? 1 : 0,
+                                                 G + (size_t)b0 * (p->n_max + 1) * 2 * p->n_rho);
+        ZM_LAUNCH_CHECK("k_recon_radial");
+    }
+    *G_out = G;
     return ZM_OK;
 }
 
 int launch_reconstruct(zm_plan_t p, const float* moments, int batch, float* out, unsigned flags,
                        cudaStream_t st) {
-    const int s = p->ws_G.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
+    float* G = nullptr;
+    const int s = launch_radial(p, moments, batch, flags, st, &G);
     if (s != ZM_OK) return s;
-    float* G = (float*)p->ws_G.ptr;
-    for (int b0 = 0; b0 < batch; b0 += 65535) {
-        const int nb = std::min(65535, batch - b0);
-        dim3 grid((p->n_rho + 127) / 128, p->n_max + 1, nb);
-        k_recon_radial<<<grid, 128, 0, st>>>(p->R32m, (const float2*)moments + (size_t)b0 * p->P, p->mrow, p->n_max,
-                                              p->n_rho, p->P, (flags & ZM_NEUMANN) ? 1 : 0,
-                                              G + (size_t)b0 * (p->n_max + 1) * 2 * p->n_rho);
-        ZM_LAUNCH_CHECK("k_recon_radial");
-    }
-    switch (p->log_theta) {
-        case 3: return launch_ifft_t<3>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 4: return launch_ifft_t<4>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 5: return launch_ifft_t<5>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 6: return launch_ifft_t<6>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 7: return launch_ifft_t<7>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 8: return launch_ifft_t<8>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 9: return launch_ifft_t<9>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 10: return launch_ifft_t<10>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        case 11: return launch_ifft_t<11>(G, p->tw, p->n_max, p->n_rho, batch, out, st);
-        default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", p->log_theta);
-    }
+    return launch_ifft<false>(p, G, batch, out, nullptr, nullptr, st);
+}
+
+__global__ void k_reduce_records(const double* __restrict__ part, int nrec, int batch, double* __restrict__ out);
+
+int launch_reconstruct_errors(zm_plan_t p, const float* moments, int batch, float* out, const float* fhat,
+                              double* err, unsigned flags, cudaStream_t st) {
+    float* G = nullptr;
+    int s = launch_radial(p, moments, batch, flags, st, &G);
+    if (s != ZM_OK) return s;
+    const int nrec = (p->n_rho + 7) / 8;
+    s = p->ws_red.grow(sizeof(double) * (size_t)batch * nrec * 4);
+    if (s != ZM_OK) return s;
+    double* part = (double*)p->ws_red.ptr;
+    s = launch_ifft<true>(p, G, batch, out, fhat, part, st);
+    if (s != ZM_OK) return s;
+    k_reduce_records<<<(batch + 3) / 4, 128, 0, st>>>(part, nrec, batch, err);
+    ZM_LAUNCH_CHECK("k_reduce_records");
+    return ZM_OK;
 }
 
 // ============================================================== pixels
@@ -367,6 +481,33 @@ __global__ void k_reduce_final(const double* __restrict__ part, int batch, int m
     }
 }
 
+// out[b] = (eps_1, eps, f_max, count) from nrec records (sd, sf, max, count)
+// per image; one warp per image.
+__global__ void k_reduce_records(const double* __restrict__ part, int nrec, int batch, double* __restrict__ out) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= batch) return;
+    double sd = 0, sf = 0, cnt = 0, mx = -INFINITY;
+    for (int j = lane; j < nrec; j += 32) {
+        const double* o = part + ((size_t)b * nrec + j) * 4;
+        sd += o[0];
+        sf += o[1];
+        mx = fmax(mx, o[2]);
+        cnt += o[3];
+    }
+    for (int o = 16; o; o >>= 1) {
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane) return;
+    out[4 * b + 0] = sd / sf;
+    out[4 * b + 1] = sd / (mx * mx * cnt);
+    out[4 * b + 2] = mx;
+    out[4 * b + 3] = cnt;
+}
+
 static int run_reduce(zm_plan_t p, int mode, const zm_image_t* ref, const zm_image_t* tst, const float* fhat,
                       const float* frec, int batch, double* out, float* mm, cudaStream_t st) {
     int s = p->ws_red.grow(sizeof(double) * (size_t)batch * RED_BLOCKS * 4);
@@ -482,6 +623,17 @@ extern "C" int zm_reconstruct(zm_plan_t plan, const float* moments, int batch, f
     if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
     DeviceGuard g(plan->device);
     return launch_reconstruct(plan, moments, batch, out, flags, (cudaStream_t)stream);
+}
+
+extern "C" int zm_reconstruct_errors(zm_plan_t plan, const float* moments, int batch, float* out,
+                                     const float* fhat, double* err, unsigned flags, void* stream) {
+    if (!plan || !moments || !fhat || !err) return set_error(ZM_EINVAL, "NULL argument");
+    if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
+    if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
+    if (!aligned8(moments) || !aligned8(fhat) || (out && !aligned8(out)))
+        return set_error(ZM_EINVAL, "moments / fhat / out must be 8-byte aligned");
+    DeviceGuard g(plan->device);
+    return launch_reconstruct_errors(plan, moments, batch, out, fhat, err, flags, (cudaStream_t)stream);
 }
 
 extern "C" int zm_reconstruct_cartesian(zm_plan_t plan, const float* moments, int batch,

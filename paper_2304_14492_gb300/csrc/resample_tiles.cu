@@ -31,6 +31,7 @@ constexpr int BOX_H = TILE + 1;          // covers y_t .. y_t + 64
 constexpr int TILE_X0 = -4;              // x_t = -4 + 64 tx (multiple of 4, as TMA needs)
 constexpr int TILE_Y0 = -1;              // y_t = -1 + 64 ty
 constexpr int TILE_MAXC = 8192;          // candidates per work item
+constexpr int TILE_MAXR = 1024;          // rings per work item
 constexpr int TILE_MAX_IMG = 64;         // tensor maps per launch
 constexpr int TILE_THREADS = 256;
 constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;
@@ -58,8 +59,13 @@ __device__ __forceinline__ unsigned long long tile_ns() {
     return t;
 }
 
+// Dynamic shared memory: the tile box, then the item's ring radii (<= TILE_MAXR)
+// and angle table (<= N entries).
 __global__ void __launch_bounds__(TILE_THREADS) k_resample_tiles(const __grid_constant__ TileParams p) {
-    __shared__ __align__(128) float tile[BOX_H * BOX_W];
+    extern __shared__ __align__(128) float tsm[];
+    float* tile = tsm;                                            // [BOX_H][BOX_W]
+    float* rad_s = tsm + BOX_H * BOX_W;                           // [TILE_MAXR]
+    float2* cs_s = reinterpret_cast<float2*>(rad_s + TILE_MAXR);  // [N]
     __shared__ __align__(8) uint64_t bar;
     const TileItem it = p.items[blockIdx.x];
     const int bl = blockIdx.y;
@@ -79,6 +85,11 @@ __global__ void __launch_bounds__(TILE_THREADS) k_resample_tiles(const __grid_co
             "l"(pol)
             : "memory");
     }
+    // while the box is in flight: this item's radii and angle table
+    const int N = p.N;
+    const int nr = it.i_hi - it.i_lo, kn = it.k_n;
+    for (int t = threadIdx.x; t < nr; t += TILE_THREADS) rad_s[t] = p.r * __ldg(&p.rho32[it.i_lo + t]);
+    for (int t = threadIdx.x; t < kn; t += TILE_THREADS) cs_s[t] = __ldg(&p.cs[(it.k_lo + t) & (N - 1)]);
     __syncthreads();
     const unsigned long long t0 = tile_ns();
     bool done = false;
@@ -105,29 +116,30 @@ __global__ void __launch_bounds__(TILE_THREADS) k_resample_tiles(const __grid_co
         return;
     }
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int N = p.N;
-    float* out = p.fhat + (size_t)(p.b_off + bl) * p.n_rho * N;
+    // candidates c = (ring ii, angle j) flattened over all lanes: ii = c / kn
+    // through a float reciprocal (exact here: c < 2^20), corrected by one step
+    float* out = p.fhat + ((size_t)(p.b_off + bl) * p.n_rho + it.i_lo) * N;
     const float xt = (float)it.x_t, yt = (float)it.y_t;
-    for (int i = it.i_lo + warp; i < it.i_hi; i += TILE_THREADS / 32) {
-        const float rad = p.r * __ldg(&p.rho32[i]);
-        float* orow = out + (size_t)i * N;
-        for (int j = lane; j < it.k_n; j += 32) {
-            const int k = (it.k_lo + j) & (N - 1);
-            const float2 c = __ldg(&p.cs[k]);
-            const float X = fmaf(rad, c.x, p.cx);
-            const float Y = fmaf(-rad, c.y, p.cy);
-            const float xf = floorf(X), yf = floorf(Y);
-            const float lxf = xf - xt, lyf = yf - yt;
-            if (lxf >= 0.f && lxf < (float)TILE && lyf >= 0.f && lyf < (float)TILE) {
-                const int lx = (int)lxf, ly = (int)lyf;
-                const float fx = X - xf, fy = Y - yf;
-                const float* t0p = tile + ly * BOX_W + lx;
-                const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
-                const float top = fmaf(fx, p01 - p00, p00);
-                const float bot = fmaf(fx, p11 - p10, p10);
-                orow[k] = fmaf(fy, bot - top, top);
-            }
+    const float inv_kn = 1.0f / (float)kn;
+    const int total = nr * kn;
+    for (int c = threadIdx.x; c < total; c += TILE_THREADS) {
+        int ii = __float2int_rd(((float)c + 0.5f) * inv_kn);
+        int j = c - ii * kn;
+        if (j >= kn) { ++ii; j -= kn; }
+        if (j < 0) { --ii; j += kn; }
+        const float rad = rad_s[ii];
+        const float2 cv = cs_s[j];
+        const float X = fmaf(rad, cv.x, p.cx);
+        const float Y = fmaf(-rad, cv.y, p.cy);
+        const float xf = floorf(X), yf = floorf(Y);
+        const int lx = (int)(xf - xt), ly = (int)(yf - yt);
+        if ((unsigned)lx < (unsigned)TILE && (unsigned)ly < (unsigned)TILE) {
+            const float fx = X - xf, fy = Y - yf;
+            const float* t0p = tile + ly * BOX_W + lx;
+            const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
+            const float top = fmaf(fx, p01 - p00, p00);
+            const float bot = fmaf(fx, p11 - p10, p10);
+            out[(size_t)ii * N + ((it.k_lo + j) & (N - 1))] = fmaf(fy, bot - top, top);
         }
     }
 }
@@ -233,7 +245,7 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
                 }
             }
             // split heavy tiles by ring ranges
-            const int per = std::max(1, TILE_MAXC / k_n);
+            const int per = std::min(TILE_MAXR, std::max(1, TILE_MAXC / k_n));
             for (int a = i_lo; a < i_hi; a += per) {
                 TileItem t{x_t, y_t, a, std::min(i_hi, a + per), k_lo, k_n};
                 items.push_back({(long)(t.i_hi - t.i_lo) * k_n, t});
@@ -308,7 +320,14 @@ int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, f
             s = encode_map(imgs[b0 + c0 + j], &tp.maps[j]);
             if (s != ZM_OK) return s;
         }
-        k_resample_tiles<<<dim3(tl->n, nc), TILE_THREADS, 0, st>>>(tp);
+        const size_t smem = sizeof(float) * (BOX_H * BOX_W + TILE_MAXR) + sizeof(float2) * (size_t)p->n_theta;
+        int dev = p->device;
+        static size_t configured[64] = {0};
+        if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
+            ZM_CUDA_TRY(cudaFuncSetAttribute(k_resample_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (dev < 64) configured[dev] = smem;
+        }
+        k_resample_tiles<<<dim3(tl->n, nc), TILE_THREADS, smem, st>>>(tp);
         ZM_LAUNCH_CHECK("k_resample_tiles");
     }
     return ZM_OK;

@@ -67,6 +67,7 @@ SIGNATURES = {
     "zm_project_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_launch_count": (ctypes.c_ulonglong, []),
     "zm_reconstruct": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_reconstruct_errors": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_uint, c_void_p]),
     "zm_reconstruct_cartesian": (c_int, [c_void_p, c_void_p, c_int, POINTER(zm_canvas_t), c_void_p, c_uint,
                                          c_void_p]),
     "zm_errors": (c_int, [c_void_p, POINTER(zm_image_t), POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
@@ -242,6 +243,11 @@ def zm_launch_count():
 
 def zm_reconstruct(plan, moments, batch, out, flags=0, stream=None):
     _check(lib().zm_reconstruct(plan, _ptr(moments), batch, _ptr(out), flags, _stream(stream)))
+
+
+def zm_reconstruct_errors(plan, moments, batch, out, fhat, err, flags=0, stream=None):
+    _check(lib().zm_reconstruct_errors(plan, _ptr(moments), batch, _ptr(out), _ptr(fhat), _ptr(err), flags,
+                                       _stream(stream)))
 
 
 def zm_reconstruct_cartesian(plan, moments, canvases, polar_tmp, flags=0, stream=None, geometries=None):

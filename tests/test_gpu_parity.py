@@ -304,6 +304,37 @@ def test_reconstruct_polar_matches_oracle(neumann, n_max, n_rho, n_theta):
     assert np.max(np.abs(out[0].double().cpu().numpy() - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("n_max,n_rho,n_theta", [(20, 32, 64), (13, 37, 32), (100, 256, 1024)])
+def test_reconstruct_errors_fused_matches_separate_and_oracle(n_max, n_rho, n_theta):
+    imgs = [synth.blob_image(2 * n_rho + 2, 2 * n_rho, 5, workload=15, index=b) for b in range(3)]
+    with Plan(n_max, n_rho, n_theta) as p:
+        out = torch.empty((3, p.P, 2), device=DEV)
+        fh = torch.empty((3, n_rho, n_theta), device=DEV)
+        zm.zm_moments_ex(p.h, [dev(i) for i in imgs], out, fh)
+        rec = torch.empty((3, n_rho, n_theta), device=DEV)
+        err_sep = torch.empty((3, 4), device=DEV, dtype=torch.float64)
+        zm.zm_reconstruct(p.h, out, 3, rec, zm.ZM_NEUMANN)
+        zm.zm_errors_polar(p.h, fh, rec, 3, err_sep)
+        rec2 = torch.empty((3, n_rho, n_theta), device=DEV)
+        err = torch.empty((3, 4), device=DEV, dtype=torch.float64)
+        zm.zm_reconstruct_errors(p.h, out, 3, rec2, fh, err, zm.ZM_NEUMANN)
+        err3 = torch.empty((3, 4), device=DEV, dtype=torch.float64)
+        zm.zm_reconstruct_errors(p.h, out, 3, None, fh, err3, zm.ZM_NEUMANN)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+    assert torch.equal(rec, rec2)
+    e1, e2, e3 = err_sep.cpu().numpy(), err.cpu().numpy(), err3.cpu().numpy()
+    assert np.array_equal(e2, e3)
+    assert np.max(np.abs(e1 - e2) / np.abs(e1)) <= 1e-5
+    f = fh.double().cpu().numpy()
+    for b in range(3):
+        r = orc.reconstruct_polar(Z[b], n_max, n_rho, n_theta, neumann=True)
+        eps1 = np.sum((f[b] - r) ** 2) / np.sum(f[b] ** 2)
+        eps = np.sum((f[b] - r) ** 2) / (f[b].max() ** 2 * f[b].size)
+        assert abs(e2[b, 0] - eps1) <= 1e-4 * eps1 and abs(e2[b, 1] - eps) <= 1e-4 * eps
+        assert e2[b, 3] == n_rho * n_theta
+
+
 def test_reconstruct_cartesian_matches_oracle():
     h, w = 60, 75
     img = synth.blob_image(h, w, 4, workload=9, index=0)
