@@ -76,22 +76,7 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
     float* rings = smem;
 
     if (MODE == KB_POLAR) {
-        if (LOGN >= 2 && (reinterpret_cast<uintptr_t>(p.fhat_in) & 15) == 0) {
-            constexpr int LOGN4 = LOGN >= 2 ? LOGN - 2 : 0;
-            for (int idx = threadIdx.x; idx < (R * N) >> 2; idx += blockDim.x) {
-                const int r = idx >> LOGN4, k4 = idx & ((N >> 2) - 1);
-                const int i = i0 + r;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < n_rho) v = __ldg(reinterpret_cast<const float4*>(p.fhat_in + ((size_t)b * n_rho + i) * N) + k4);
-                *reinterpret_cast<float4*>(rings + r * ROW + 4 * k4) = v;
-            }
-        } else {
-            for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-                const int r = idx >> LOGN, k = idx & (N - 1);
-                const int i = i0 + r;
-                rings[r * ROW + k] = (i < n_rho) ? __ldg(&p.fhat_in[((size_t)b * n_rho + i) * N + k]) : 0.f;
-            }
-        }
+        // samples go straight from global memory into the FFT registers below
     } else {
         const GeoImage im = p.img[bl];
 #pragma unroll 4
@@ -109,19 +94,38 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
         }
     }
     if (MODE == KB_RESAMPLE) return;
-    __syncthreads();
-
     const int n_max = p.n_max;
     float* Fs = smem + R * ROW;                  // [2][n_max+1][R]
+    float2* twt = reinterpret_cast<float2*>(smem + ((R * ROW + 2 * (n_max + 1) * R + 1) & ~1));
+    FFT::load_twiddles(twt, p.tw);
+    __syncthreads();
+
     {
         float* row = rings + warp * ROW;
         float2 v[FFT::Q];
-        const float2* z = reinterpret_cast<const float2*>(row);
+        if (MODE == KB_POLAR) {
+            const int i = i0 + warp;
+            const bool live = lane < FFT::L && i < n_rho;
+            const float* src = p.fhat_in + ((size_t)b * n_rho + (live ? i : 0)) * N;
+            if ((reinterpret_cast<uintptr_t>(p.fhat_in) & 7) == 0) {
+                const float2* z = reinterpret_cast<const float2*>(src);
 #pragma unroll
-        for (int s = 0; s < FFT::Q; ++s)
-            v[s] = (lane < FFT::L) ? z[lane + FFT::L * s] : make_float2(0.f, 0.f);
-        __syncwarp();
-        FFT::forward(v, lane, p.tw);
+                for (int s = 0; s < FFT::Q; ++s) v[s] = live ? __ldg(&z[lane + FFT::L * s]) : make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int s = 0; s < FFT::Q; ++s) {
+                    const int j = lane + FFT::L * s;
+                    v[s] = live ? make_float2(__ldg(src + 2 * j), __ldg(src + 2 * j + 1)) : make_float2(0.f, 0.f);
+                }
+            }
+        } else {
+            const float2* z = reinterpret_cast<const float2*>(row);
+#pragma unroll
+            for (int s = 0; s < FFT::Q; ++s)
+                v[s] = (lane < FFT::L) ? z[lane + FFT::L * s] : make_float2(0.f, 0.f);
+            __syncwarp();
+        }
+        FFT::forward(v, lane, twt);
         float2* X = reinterpret_cast<float2*>(row);
         if (lane < FFT::L) {
 #pragma unroll
@@ -157,7 +161,8 @@ template <int LOGN, int MODE>
 static int launch_kb_t(const KbParams& kp, int R, int nb, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const size_t smem = sizeof(float) * ((size_t)R * FFT::ROW_FLOATS +
-                                         (MODE == KB_RESAMPLE ? 0 : (size_t)2 * (kp.n_max + 1) * R));
+                                         (MODE == KB_RESAMPLE ? 0 : (size_t)2 * (kp.n_max + 1) * R + 2)) +
+                        (MODE == KB_RESAMPLE ? 0 : sizeof(float2) * (size_t)FFT::TW_FLOAT2);
     int dev = 0;
     cudaGetDevice(&dev);
     static size_t configured[64] = {0};

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant
     uint8_t* alo = ahi + p.ntmax * TC_KC * 2;
     uint64_t* bar = reinterpret_cast<uint64_t*>(alo + p.ntmax * TC_KC * 2);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    volatile int* okflag = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int m = blockIdx.x;
     const int col0 = blockIdx.y * TC_M;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant
     const int rowbase = p.mrow[m];
     const int ib = s * p.chunk;
     const int ie = min(p.n_rho, ib + p.chunk);
+    const int vrows = min(TC_M, p.ncol - col0);             // real columns in this tile
     const int n_tiles = (Km + TC_NMAX - 1) / TC_NMAX;
     const int nt_max = min(Km, TC_NMAX);
     const int NTa = ((nt_max + 15) / 16) * 16;             // MMA N of the widest tile
@@ -174,13 +176,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant
         const uint32_t idesc = instr_desc(NT, p.fp16);
         int first = 1;
         for (int k0 = ib; k0 < ie && ok; k0 += TC_KC) {
-            // F chunk -> hi / lo tiles (128 rows x 64 k)
-            for (int task = tid; task < TC_M * 8; task += TC_THREADS) {
+            // F chunk -> hi / lo tiles: only the rows of real columns.  Rows past
+            // the batch keep stale values; D rows are independent, so they only
+            // produce D rows that are never read.
+            for (int task = tid; task < vrows * 8; task += TC_THREADS) {
                 const int row = task >> 3, g = task & 7;
                 const int col = col0 + row;
                 const int kk = k0 + g * 8;
                 float x[8];
-                if (col < p.ncol) {
+                {
                     const float* src = Fm + (size_t)col * p.n_rho + kk;
                     if (fvec && kk + 8 <= ie) {
                         const float4 a = __ldg(reinterpret_cast<const float4*>(src));
@@ -191,11 +195,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant
 #pragma unroll
                         for (int e = 0; e < 8; ++e) x[e] = (kk + e < ie) ? __ldg(src + e) : 0.f;
                     }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] = 0.f;
                 }
-                const float fs = (col < p.ncol) ? column_scale(p.colmax, col) : 1.f;
+                const float fs = column_scale(p.colmax, col);
                 uint16_t h[8], l[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) split2(x[e] * fs, p.fp16, &h[e], &l[e]);
@@ -208,14 +209,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant
                 *reinterpret_cast<uint4*>(fhi + o) = vh;
                 *reinterpret_cast<uint4*>(flo + o) = vl;
             }
-            // A chunk (hi / lo, NT rows x 64 k)
-            for (int task = tid; task < NT * 8 * 2; task += TC_THREADS) {
-                const int half = task >= NT * 8;
-                const int t2 = half ? task - NT * 8 : task;
+            // A chunk (hi / lo): rows past K_m likewise only feed unread D columns
+            for (int task = tid; task < nrow * 8 * 2; task += TC_THREADS) {
+                const int half = task >= nrow * 8;
+                const int t2 = half ? task - nrow * 8 : task;
                 const int row = t2 >> 3, g = t2 & 7;
                 const int kk = k0 + g * 8;
                 uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (row < nrow) {
+                {
                     const uint16_t* src = (half ? p.Alo : p.Ahi) + (size_t)(rowbase + n0 + row) * p.n_rho + kk;
                     if (avec && kk + 8 <= ie) {
                         v = __ldg(reinterpret_cast<const uint4*>(src));
@@ -258,12 +259,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_tc(const __grid_constant
                              : "memory");
             }
             first = 0;
-            // the tiles are rewritten next chunk: wait for the MMAs to finish reading them
-            bool done = mbar_wait(bar_a, phase, t0);
+            // the tiles are rewritten next chunk: one thread waits for the MMAs to
+            // finish reading them, the others wait at the barrier
+            if (tid == 0) {
+                const bool done = mbar_wait(bar_a, phase, t0);
+                *okflag = done ? 1 : 0;
+                if (!done) atomicExch(p.status, ZM_ETIMEOUT);
+            }
             phase ^= 1u;
+            __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            ok = __syncthreads_and(done) != 0;          // one decision for the whole CTA
-            if (!ok && tid == 0) atomicExch(p.status, ZM_ETIMEOUT);
+            ok = *okflag != 0;
         }
         if (!ok) break;
         // epilogue: lanes 32w..32w+31 of TMEM = D rows (image columns)
@@ -345,9 +351,11 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
     }
     const int ctiles = (ncol + TC_M - 1) / TC_M;
     const int base = (p->n_max + 1) * ctiles;
-    const int target = 3 * num_sms_tc(p->device);
+    // enough CTAs to cover the load -> MMA latency: up to one 64-wide chunk of
+    // the radial index per CTA, at most 32 slices
+    const int target = 8 * num_sms_tc(p->device);
     const int kchunks = (p->n_rho + TC_KC - 1) / TC_KC;
-    int S = std::max(1, std::min(kchunks, (target + base - 1) / base));
+    int S = std::max(1, std::min(std::min(kchunks, 32), (target + base - 1) / base));
     const int chunk = ((kchunks + S - 1) / S) * TC_KC;
     S = (p->n_rho + chunk - 1) / chunk;
     s = p->ws_part.grow(sizeof(float) * (size_t)S * p->P * ncol);

@@ -39,8 +39,25 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
     float re[RB], im[RB];
 #pragma unroll
     for (int bb = 0; bb < RB; ++bb) re[bb] = im[bb] = 0.f;
-    for (int j = 0; j < Km; ++j) {
-        const float r = __ldg(&R32m[(size_t)(row0 + j) * n_rho + i]);
+    // eight table loads in flight per step: the loop is bound by their latency otherwise
+    const float* Rcol = R32m + (size_t)row0 * n_rho + i;
+    int j = 0;
+    for (; j + 8 <= Km; j += 8) {
+        float r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r[u] = __ldg(Rcol + (size_t)(j + u) * n_rho);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+            for (int bb = 0; bb < RB; ++bb) {
+                const float2 z = zs[bb * Km + j + u];
+                re[bb] = fmaf(r[u], z.x, re[bb]);
+                im[bb] = fmaf(r[u], z.y, im[bb]);
+            }
+        }
+    }
+    for (; j < Km; ++j) {
+        const float r = __ldg(Rcol + (size_t)j * n_rho);
 #pragma unroll
         for (int bb = 0; bb < RB; ++bb) {
             const float2 z = zs[bb * Km + j];
@@ -64,28 +81,33 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // spectrum S (S_0 = 2 Re G_0, S_m = G_m, S_{N-m} = conj G_m) and
 // x_k = sum_m S_m e^{2 pi i m k/N} = 2 f~_k, the packed z_j = x_{2j} + i x_{2j+1}
 // is the M-point inverse DFT of
-//   C_m = (S_m + conj S_{M-m}) + i e^{2 pi i m/N} (S_m - conj S_{M-m}),
-// computed as conj(DFT(conj C)) by the same warp FFT as the forward path.
+//   C_m = (S_m + conj S_{M-m}) + i e^{2 pi i m/N} (S_m - conj S_{M-m}).
+// One warp per ring: C is formed straight from G in shared memory in the
+// order inverse_natural() wants, and its output is already in natural order
+// across lanes, so f~ is written (and the reference read) with coalesced
+// accesses from registers.
 // With ERR, the CTA also accumulates, against the reference polar samples
 // `ref`, sum (ref - f~)^2, sum ref^2, max ref and the node count over its rings
 // into one record part[b][blockIdx.x] (Eq. 10 / Eq. 13 on the polar nodes); `out`
 // may then be NULL.
 template <int LOGN, bool ERR>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(256)
 k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho,
              float* __restrict__ out, const float* __restrict__ ref, double* __restrict__ part) {
     using FFT = RingFFT<LOGN>;
     constexpr int N = FFT::N;
     constexpr int M = FFT::M;
-    constexpr int ROW = FFT::ROW_FLOATS;
-    extern __shared__ __align__(16) float smem[];
+    constexpr int L = FFT::L;
+    constexpr int Q = FFT::Q;
+    extern __shared__ __align__(16) float2 Gs[];              // [R][n_max+1]
+    __shared__ float red[8][4];
     const int R = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.y;
     const int i0 = blockIdx.x * R;
-    float* rows = smem;                                         // [R][ROW]
-    float2* Gs = reinterpret_cast<float2*>(smem + R * ROW);     // [R][n_max+1]
     const int nm1 = n_max + 1;
+    float2* twt = Gs + R * nm1;
+    FFT::load_twiddles(twt, tw);
     for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
         const int r = e % R, m = e / R;
         const int i = i0 + r;
@@ -98,10 +120,11 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     }
     __syncthreads();
     const float2* Gr = Gs + warp * nm1;
-    float2 v[FFT::Q];
+    const int cidx = FFT::brev_lane(lane & (L - 1));
+    float2 v[Q];
 #pragma unroll
-    for (int s = 0; s < FFT::Q; ++s) {
-        const int m = (lane & (FFT::L - 1)) + FFT::L * s;
+    for (int a = 0; a < Q; ++a) {
+        const int m = a + Q * cidx;
         float2 Sm = make_float2(0.f, 0.f), T = make_float2(0.f, 0.f);
         if (m <= n_max) Sm = (m == 0) ? make_float2(2.f * Gr[0].x, 0.f) : Gr[m];
         const int q = M - m;
@@ -109,33 +132,33 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
         const float2 w = __ldg(&tw[m]);                  // e^{-2 pi i m/N}
         const float2 ie = make_float2(w.y, w.x);         // i e^{+2 pi i m/N} = i conj(w)
         const float2 C = cadd(cadd(Sm, T), cmul(ie, csub(Sm, T)));
-        v[s] = (lane < FFT::L) ? cconj(C) : make_float2(0.f, 0.f);
+        v[a] = (lane < L) ? C : make_float2(0.f, 0.f);
     }
-    FFT::forward(v, lane, tw);
-    float2* X = reinterpret_cast<float2*>(rows + warp * ROW);
-    if (lane < FFT::L) {
-#pragma unroll
-        for (int r = 0; r < FFT::Q; ++r)
-            X[FFT::pad(FFT::out_index(r, lane))] = make_float2(0.5f * v[r].x, -0.5f * v[r].y);
-    }
-    __syncwarp();
+    FFT::inverse_natural(v, lane, twt);
     const int i = i0 + warp;
     float sd = 0.f, sf = 0.f, mx = -INFINITY, cnt = 0.f;
-    if (i < n_rho) {
+    if (i < n_rho && lane < L) {
         const size_t row = ((size_t)b * n_rho + i) * N;
         float2* o = out ? reinterpret_cast<float2*>(out + row) : nullptr;
-        const float2* rf = ERR ? reinterpret_cast<const float2*>(ref + row) : nullptr;
-        for (int j = lane; j < M; j += 32) {
-            const float2 x = X[FFT::pad(j)];
-            if (o) o[j] = x;
-            if (ERR) {
-                const float2 f = __ldg(&rf[j]);
-                const float d0 = f.x - x.x, d1 = f.y - x.y;
+        if (ERR) {
+            const float2* rf = reinterpret_cast<const float2*>(ref + row);
+            float2 f[Q];
+#pragma unroll
+            for (int r = 0; r < Q; ++r) f[r] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r)]);
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
+                if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
+                const float d0 = f[r].x - x.x, d1 = f[r].y - x.y;
                 sd = fmaf(d0, d0, fmaf(d1, d1, sd));
-                sf = fmaf(f.x, f.x, fmaf(f.y, f.y, sf));
-                mx = fmaxf(mx, fmaxf(f.x, f.y));
+                sf = fmaf(f[r].x, f[r].x, fmaf(f[r].y, f[r].y, sf));
+                mx = fmaxf(mx, fmaxf(f[r].x, f[r].y));
                 cnt += 2.f;
             }
+        } else {
+#pragma unroll
+            for (int r = 0; r < Q; ++r)
+                o[lane + L * brev_c<FFT::LOGQ>(r)] = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
         }
     }
     if (ERR) {
@@ -145,23 +168,21 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
             cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
         }
-        __syncthreads();                                  // the rows are free again: reuse as scratch
-        float* red = smem;
         if (lane == 0) {
-            red[4 * warp + 0] = sd;
-            red[4 * warp + 1] = sf;
-            red[4 * warp + 2] = mx;
-            red[4 * warp + 3] = cnt;
+            red[warp][0] = sd;
+            red[warp][1] = sf;
+            red[warp][2] = mx;
+            red[warp][3] = cnt;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double a = 0, c = 0, n = 0;
             float m = -INFINITY;
             for (int w = 0; w < R; ++w) {
-                a += red[4 * w];
-                c += red[4 * w + 1];
-                m = fmaxf(m, red[4 * w + 2]);
-                n += red[4 * w + 3];
+                a += red[w][0];
+                c += red[w][1];
+                m = fmaxf(m, red[w][2]);
+                n += red[w][3];
             }
             double* o = part + ((size_t)b * gridDim.x + blockIdx.x) * 4;
             o[0] = a;
@@ -177,7 +198,7 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
                          const float* ref, double* part, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const int R = 8;
-    const size_t smem = sizeof(float) * (size_t)R * FFT::ROW_FLOATS + sizeof(float2) * (size_t)R * (n_max + 1);
+    const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2);
     int dev = 0;
     cudaGetDevice(&dev);
     static size_t configured[64] = {0};

@@ -4,12 +4,14 @@
 // corner ("anchor") is (floor X, floor Y).  The anchor plane is cut into 64x64
 // tiles; a work item is one tile plus the ring and angle ranges whose samples
 // can anchor in it (computed on the host from the geometry, with margins).
-// A CTA loads its tile and a one-pixel halo (a 68x65 box, zero outside the
-// image) with one TMA copy, evaluates the candidate samples, keeps those whose
-// anchor lies in the tile and writes them to f_hat[b][i][k].  Each image pixel
-// is read from HBM once and every gather is a shared-memory access; each
-// sample is claimed by exactly one tile because all tiles evaluate its
-// coordinates with the same float arithmetic.
+// Which samples a tile owns depends only on the geometry, so k_tile_plan
+// decides it once per geometry (from the candidates' anchors, computed with the
+// same float arithmetic as every later pass, so the tiles partition the samples
+// exactly) and stores them as packed (ring, angle) indices.  Per frame, a CTA
+// loads its tile and a one-pixel halo (a 68x65 box, zero outside the image) with
+// one TMA copy and interpolates exactly its own samples from shared memory into
+// f_hat[b][i][k].  Each image pixel is read from HBM once and every gather is a
+// shared-memory access.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -42,8 +44,14 @@ struct TileItem {
     int k_lo, k_n;       // angles (k_lo + j) mod N, j < k_n; k_lo in [0, N)
 };
 
+// Packed sample of a work item: (ring offset << 11) | angle offset in the
+// item's staged angle window (ring offset < 1024, angle offset < 2048).
+constexpr int SAMPLE_KBITS = 11;
+
 struct TileParams {
     const TileItem* items;
+    const uint32_t* samples;     // packed samples of all items
+    const int* item_off;         // [n_items + 1] first sample of each item
     const float* rho32;
     const float2* cs;
     float* fhat;
@@ -57,6 +65,85 @@ __device__ __forceinline__ unsigned long long tile_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
+}
+
+// Sample coordinates: the single definition every pass uses.
+__device__ __forceinline__ void sample_xy(float rad, float2 cv, float cx, float cy, float* X, float* Y) {
+    *X = fmaf(rad, cv.x, cx);
+    *Y = fmaf(-rad, cv.y, cy);
+}
+
+// Planning pass over the candidate (ring, angle) pairs of each item: keeps
+// those whose anchor lies in the item's tile.  count_only: counts[item];
+// otherwise writes the packed samples in candidate order from item_off[item].
+struct PlanParams {
+    const TileItem* items;
+    const float* rho32;
+    const float2* cs;
+    int* counts;
+    const int* item_off;
+    uint32_t* samples;
+    int N;
+    float cx, cy, r;
+    int count_only;
+};
+
+__global__ void __launch_bounds__(TILE_THREADS) k_tile_plan(const __grid_constant__ PlanParams p) {
+    __shared__ int warp_tot[TILE_THREADS / 32];
+    __shared__ int base_s;
+    const TileItem it = p.items[blockIdx.x];
+    const int N = p.N;
+    const int nr = it.i_hi - it.i_lo, kn = it.k_n;
+    const int total = nr * kn;
+    const float xt = (float)it.x_t, yt = (float)it.y_t;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int mine = 0;
+    if (threadIdx.x == 0) base_s = p.count_only ? 0 : p.item_off[blockIdx.x];
+    __syncthreads();
+    for (int c0 = 0; c0 < total; c0 += TILE_THREADS) {
+        const int c = c0 + threadIdx.x;
+        bool valid = false;
+        int ii = 0, j = 0;
+        if (c < total) {
+            ii = c / kn;
+            j = c - ii * kn;
+            const float rad = p.r * __ldg(&p.rho32[it.i_lo + ii]);
+            const float2 cv = __ldg(&p.cs[(it.k_lo + j) & (N - 1)]);
+            float X, Y;
+            sample_xy(rad, cv, p.cx, p.cy, &X, &Y);
+            const int lx = (int)(floorf(X) - xt), ly = (int)(floorf(Y) - yt);
+            valid = (unsigned)lx < (unsigned)TILE && (unsigned)ly < (unsigned)TILE;
+        }
+        if (p.count_only) {
+            mine += valid ? 1 : 0;
+            continue;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, valid);
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) {
+            before += (w < warp) ? warp_tot[w] : 0;
+            all += warp_tot[w];
+        }
+        if (valid) {
+            const int pos = base_s + before + __popc(bal & ((1u << lane) - 1u));
+            p.samples[pos] = ((uint32_t)ii << SAMPLE_KBITS) | (uint32_t)j;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_s += all;
+        __syncthreads();
+    }
+    if (p.count_only) {
+        for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if (lane == 0) warp_tot[warp] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < TILE_THREADS / 32; ++w) t += warp_tot[w];
+            p.counts[blockIdx.x] = t;
+        }
+    }
 }
 
 // Dynamic shared memory: the tile box, then the item's ring radii (<= TILE_MAXR)
@@ -90,57 +177,55 @@ __global__ void __launch_bounds__(TILE_THREADS) k_resample_tiles(const __grid_co
     const int nr = it.i_hi - it.i_lo, kn = it.k_n;
     for (int t = threadIdx.x; t < nr; t += TILE_THREADS) rad_s[t] = p.r * __ldg(&p.rho32[it.i_lo + t]);
     for (int t = threadIdx.x; t < kn; t += TILE_THREADS) cs_s[t] = __ldg(&p.cs[(it.k_lo + t) & (N - 1)]);
-    __syncthreads();
-    const unsigned long long t0 = tile_ns();
-    bool done = false;
-    while (!done) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
-            : "=r"(ok) : "r"(bar_a) : "memory");
-        done = ok != 0;
-        if (!done && tile_ns() - t0 > TILE_WAIT_NS) break;
-    }
-    if (!__syncthreads_and(done)) {
-        // the copy did not arrive in time: report it, let it drain (bounded), leave
-        if (threadIdx.x == 0) {
+    // one thread waits for the box (bounded); the others wait at the barrier
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = tile_ns();
+        uint32_t ok = 0;
+        while (!ok) {
+            asm volatile(
+                "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
+                : "=r"(ok) : "r"(bar_a) : "memory");
+            if (!ok && tile_ns() - t0 > TILE_WAIT_NS) break;
+        }
+        if (!ok) {
+            // the copy did not arrive in time: report it and let it drain (bounded)
             atomicExch(p.status, ZM_ETIMEOUT);
             const unsigned long long t1 = tile_ns();
-            uint32_t ok = 0;
-            while (!ok && tile_ns() - t1 < TILE_WAIT_NS)
+            uint32_t late = 0;
+            while (!late && tile_ns() - t1 < TILE_WAIT_NS)
                 asm volatile(
                     "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
-                    : "=r"(ok) : "r"(bar_a) : "memory");
+                    : "=r"(late) : "r"(bar_a) : "memory");
         }
-        __syncthreads();
-        return;
+        s_ok = ok ? 1 : 0;
     }
+    __syncthreads();
+    if (!s_ok) return;
 
-    // candidates c = (ring ii, angle j) flattened over all lanes: ii = c / kn
-    // through a float reciprocal (exact here: c < 2^20), corrected by one step
+    // exactly the samples this tile owns (planned once per geometry)
     float* out = p.fhat + ((size_t)(p.b_off + bl) * p.n_rho + it.i_lo) * N;
     const float xt = (float)it.x_t, yt = (float)it.y_t;
-    const float inv_kn = 1.0f / (float)kn;
-    const int total = nr * kn;
-    for (int c = threadIdx.x; c < total; c += TILE_THREADS) {
-        int ii = __float2int_rd(((float)c + 0.5f) * inv_kn);
-        int j = c - ii * kn;
-        if (j >= kn) { ++ii; j -= kn; }
-        if (j < 0) { --ii; j += kn; }
-        const float rad = rad_s[ii];
-        const float2 cv = cs_s[j];
-        const float X = fmaf(rad, cv.x, p.cx);
-        const float Y = fmaf(-rad, cv.y, p.cy);
+    const int s0 = p.item_off[blockIdx.x];
+    const int cnt = p.item_off[blockIdx.x + 1] - s0;
+    const uint32_t* smp = p.samples + s0;
+    for (int c = threadIdx.x; c < cnt; c += TILE_THREADS) {
+        const uint32_t code = __ldg(&smp[c]);
+        const int ii = (int)(code >> SAMPLE_KBITS);
+        const int j = (int)(code & ((1u << SAMPLE_KBITS) - 1u));
+        float X, Y;
+        sample_xy(rad_s[ii], cs_s[j], p.cx, p.cy, &X, &Y);
         const float xf = floorf(X), yf = floorf(Y);
-        const int lx = (int)(xf - xt), ly = (int)(yf - yt);
-        if ((unsigned)lx < (unsigned)TILE && (unsigned)ly < (unsigned)TILE) {
-            const float fx = X - xf, fy = Y - yf;
-            const float* t0p = tile + ly * BOX_W + lx;
-            const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
-            const float top = fmaf(fx, p01 - p00, p00);
-            const float bot = fmaf(fx, p11 - p10, p10);
-            out[(size_t)ii * N + ((it.k_lo + j) & (N - 1))] = fmaf(fy, bot - top, top);
-        }
+        // the plan put this sample here, so its anchor is inside the tile; the
+        // clamp only keeps shared-memory reads in the box should that ever fail
+        const int lx = min(max((int)(xf - xt), 0), TILE - 1);
+        const int ly = min(max((int)(yf - yt), 0), TILE - 1);
+        const float fx = X - xf, fy = Y - yf;
+        const float* t0p = tile + ly * BOX_W + lx;
+        const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
+        const float top = fmaf(fx, p01 - p00, p00);
+        const float bot = fmaf(fx, p11 - p10, p10);
+        out[(size_t)ii * N + ((it.k_lo + j) & (N - 1))] = fmaf(fy, bot - top, top);
     }
 }
 
@@ -180,9 +265,16 @@ static int encode_map(const zm_image_t& im, CUtensorMap* map) {
 
 struct TileList {
     TileItem* items = nullptr;
+    uint32_t* samples = nullptr;   // packed samples, item after item
+    int* item_off = nullptr;       // [n + 1]
     int n = 0;
+    long long n_samples = 0;
     bool need_zero = false;   // some samples anchor outside every tile (they are 0)
-    ~TileList() { if (items) cudaFree(items); }
+    ~TileList() {
+        if (items) cudaFree(items);
+        if (samples) cudaFree(samples);
+        if (item_off) cudaFree(item_off);
+    }
 };
 
 // Work items for one geometry.  Ring range from the distance range of the
@@ -256,10 +348,41 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
     std::vector<TileItem> h(items.size());
     for (size_t j = 0; j < items.size(); ++j) h[j] = items[j].second;
     tl->n = (int)h.size();
-    if (tl->n) {
-        ZM_CUDA_TRY(cudaMalloc(&tl->items, sizeof(TileItem) * h.size()));
-        ZM_CUDA_TRY(cudaMemcpy(tl->items, h.data(), sizeof(TileItem) * h.size(), cudaMemcpyHostToDevice));
-    }
+    if (!tl->n) return ZM_OK;
+    ZM_CUDA_TRY(cudaMalloc(&tl->items, sizeof(TileItem) * h.size()));
+    ZM_CUDA_TRY(cudaMemcpy(tl->items, h.data(), sizeof(TileItem) * h.size(), cudaMemcpyHostToDevice));
+    // plan: count the samples each tile owns, then store them packed
+    PlanParams pp;
+    pp.items = tl->items;
+    pp.rho32 = p->rho32;
+    pp.cs = p->cs;
+    pp.N = N;
+    pp.cx = g.cx;
+    pp.cy = g.cy;
+    pp.r = g.r;
+    ZM_CUDA_TRY(cudaMalloc(&pp.counts, sizeof(int) * tl->n));
+    pp.item_off = nullptr;
+    pp.samples = nullptr;
+    pp.count_only = 1;
+    k_tile_plan<<<tl->n, TILE_THREADS>>>(pp);
+    cudaError_t ce = cudaGetLastError();
+    std::vector<int> cnt(tl->n);
+    if (ce == cudaSuccess) ce = cudaMemcpy(cnt.data(), pp.counts, sizeof(int) * tl->n, cudaMemcpyDeviceToHost);
+    cudaFree(pp.counts);
+    if (ce != cudaSuccess) return cuda_error(ce, "k_tile_plan (count)");
+    count_launch();
+    std::vector<int> off(tl->n + 1, 0);
+    for (int j = 0; j < tl->n; ++j) off[j + 1] = off[j] + cnt[j];
+    tl->n_samples = off[tl->n];
+    ZM_CUDA_TRY(cudaMalloc(&tl->item_off, sizeof(int) * (tl->n + 1)));
+    ZM_CUDA_TRY(cudaMemcpy(tl->item_off, off.data(), sizeof(int) * (tl->n + 1), cudaMemcpyHostToDevice));
+    ZM_CUDA_TRY(cudaMalloc(&tl->samples, sizeof(uint32_t) * std::max<long long>(1, tl->n_samples)));
+    pp.item_off = tl->item_off;
+    pp.samples = tl->samples;
+    pp.count_only = 0;
+    k_tile_plan<<<tl->n, TILE_THREADS>>>(pp);
+    ZM_LAUNCH_CHECK("k_tile_plan");
+    ZM_CUDA_TRY(cudaDeviceSynchronize());
     return ZM_OK;
 }
 
@@ -304,6 +427,8 @@ int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, f
     if (tl->n == 0) return ZM_OK;
     static thread_local TileParams tp;
     tp.items = tl->items;
+    tp.samples = tl->samples;
+    tp.item_off = tl->item_off;
     tp.rho32 = p->rho32;
     tp.cs = p->cs;
     tp.fhat = fhat;

@@ -47,15 +47,41 @@ struct RingFFT {
     static_assert(ROW_FLOATS % 4 == 0, "ring rows must stay 16-byte aligned");
     static_assert(2 * (M + (M - 1) / 16) <= ROW_FLOATS, "padded spectrum must fit the row");
 
+    // Twiddles used by one warp FFT, staged once per CTA in shared memory:
+    //   t1[x]         = W_Q^x,               x < Q/2   (in-register stages)
+    //   t2[k1 * L + t] = W_M^{t k1},          k1 < Q    (between the stages)
+    //   t3[e * L + t]  = W_{2h}^{t mod h},    h = 2^e   (cross-lane stages)
+    // with W_n = e^{-2 pi i / n}; the inverse uses their conjugates.
+    static constexpr int TW_T1 = Q / 2 > 0 ? Q / 2 : 1;
+    static constexpr int TW_FLOAT2 = TW_T1 + Q * L + (LOGL > 0 ? LOGL : 1) * L;
+
+    __device__ static __forceinline__ void load_twiddles(float2* tab, const float2* __restrict__ tw) {
+        float2* t1 = tab;
+        float2* t2 = tab + TW_T1;
+        float2* t3 = t2 + Q * L;
+        for (int x = threadIdx.x; x < Q / 2; x += blockDim.x) t1[x] = __ldg(&tw[x * (N / Q)]);
+        for (int e = threadIdx.x; e < Q * L; e += blockDim.x) {
+            const int k1 = e / L, t = e - k1 * L;
+            t2[e] = __ldg(&tw[2 * t * k1]);
+        }
+        for (int e = threadIdx.x; e < LOGL * L; e += blockDim.x) {
+            const int lg = e / L, t = e - lg * L;
+            const int h = 1 << lg;
+            t3[e] = __ldg(&tw[(t & (h - 1)) * (N / (2 * h))]);
+        }
+    }
+
     __device__ static __forceinline__ int pad(int j) { return j + (j >> 4); }
     __device__ static __forceinline__ int brev_lane(int t) {
         return LOGL == 0 ? 0 : (int)(__brev((unsigned)t) >> (32 - LOGL));
     }
 
-    // Forward DFT X_k = sum_j z_j e^{-2 pi i j k / M}.  `tw` holds
-    // e^{-2 pi i j / N}, j = 0..N-1 (so W_M^x = tw[2x]).  All 32 lanes must
-    // call; lanes >= L carry dummy data.
-    __device__ static __forceinline__ void forward(float2 (&v)[Q], int t, const float2* __restrict__ tw) {
+    // Forward DFT X_k = sum_j z_j e^{-2 pi i j k / M}; `tab` from
+    // load_twiddles().  All 32 lanes must call; lanes >= L carry dummy data.
+    __device__ static __forceinline__ void forward(float2 (&v)[Q], int t, const float2* tab) {
+        const float2* t1 = tab;
+        const float2* t2 = tab + TW_T1;
+        const float2* t3 = t2 + Q * L;
 #pragma unroll
         for (int h = Q / 2; h >= 1; h >>= 1) {
 #pragma unroll
@@ -65,26 +91,66 @@ struct RingFFT {
                     const float2 x = v[b + j], y = v[b + j + h];
                     v[b + j] = cadd(x, y);
                     const float2 d = csub(x, y);
-                    v[b + j + h] = (j == 0) ? d : cmul(d, __ldg(&tw[j * (N / (2 * h))]));
+                    v[b + j + h] = (j == 0) ? d : cmul(d, t1[j * (Q / (2 * h))]);
                 }
             }
         }
         const int tl = t & (L - 1);
 #pragma unroll
-        for (int r = 1; r < Q; ++r) {
-            const int k1 = brev_c<LOGQ>(r);
-            v[r] = cmul(v[r], __ldg(&tw[2 * tl * k1]));
-        }
+        for (int r = 1; r < Q; ++r) v[r] = cmul(v[r], t2[brev_c<LOGQ>(r) * L + tl]);
 #pragma unroll
-        for (int h = L / 2; h >= 1; h >>= 1) {
+        for (int lg = LOGL - 1; lg >= 0; --lg) {
+            const int h = 1 << lg;
             const bool upper = (t & h) != 0;
-            const float2 w = __ldg(&tw[(t & (h - 1)) * (N / (2 * h))]);
+            const float2 w = t3[lg * L + tl];
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 float2 p;
                 p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
                 p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
                 v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
+            }
+        }
+    }
+
+    // Inverse DFT z_j = sum_m C_m e^{+2 pi i j m / M} in the transposed
+    // structure: on entry lane l, register a holds C[a + Q brev_L(l)]; on exit
+    // lane t, register r holds z[t + L brev_Q(r)] (natural order across lanes).
+    // With m = a + Q c and j = t + L s:
+    //   z[t + L s] = sum_a e^{2 pi i a s / Q} e^{2 pi i a t / M} sum_c C[a + Q c] e^{2 pi i c t / L},
+    // i.e. an L-point DFT across lanes (decimation in time, bit-reversed input),
+    // a twiddle, and a Q-point DFT in registers (decimation in frequency).
+    __device__ static __forceinline__ void inverse_natural(float2 (&v)[Q], int t, const float2* tab) {
+        const float2* t1 = tab;
+        const float2* t2 = tab + TW_T1;
+        const float2* t3 = t2 + Q * L;
+        const int tl = t & (L - 1);
+#pragma unroll
+        for (int lg = 0; lg < LOGL; ++lg) {
+            const int h = 1 << lg;
+            const bool upper = (t & h) != 0;
+            const float2 w = cconj(t3[lg * L + tl]);
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                float2 p;
+                p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
+                p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
+                v[r] = upper ? csub(p, cmul(w, v[r])) : cadd(v[r], cmul(w, p));
+            }
+        }
+#pragma unroll
+        for (int a = 1; a < Q; ++a) v[a] = cmul(v[a], cconj(t2[a * L + tl]));
+#pragma unroll
+        for (int h = Q / 2; h >= 1; h >>= 1) {
+#pragma unroll
+            for (int b = 0; b < Q; b += 2 * h) {
+#pragma unroll
+                for (int j = 0; j < h; ++j) {
+                    const float2 x = v[b + j], y = v[b + j + h];
+                    v[b + j] = cadd(x, y);
+                    const float2 d = csub(x, y);
+                    v[b + j + h] = (j == 0) ? d : cmul(d, cconj(t1[j * (Q / (2 * h))]));
+                }
             }
         }
     }
