@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
     const int n_max = p.n_max;
     float* Fs = smem + R * ROW;                  // [2][n_max+1][R]
     float2* twt = reinterpret_cast<float2*>(smem + ((R * ROW + 2 * (n_max + 1) * R + 1) & ~1));
+    float2* twm = twt + FFT::TW_FLOAT2;            // e^{-2 pi i m / N}, m <= n_max
     FFT::load_twiddles(twt, p.tw);
+    for (int m = threadIdx.x; m <= n_max; m += blockDim.x) twm[m] = __ldg(&p.tw[m]);
     __syncthreads();
 
     {
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
             const float2 E = cscale(cadd(A, B), 0.5f);
             const float2 D = csub(A, B);
             const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-            const float2 Fm = cadd(E, cmul(__ldg(&p.tw[m]), O));
+            const float2 Fm = cadd(E, cmul(twm[m], O));
             Fs[m * R + warp] = Fm.x;
             Fs[((n_max + 1) + m) * R + warp] = Fm.y;
         }
@@ -162,7 +164,7 @@ static int launch_kb_t(const KbParams& kp, int R, int nb, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const size_t smem = sizeof(float) * ((size_t)R * FFT::ROW_FLOATS +
                                          (MODE == KB_RESAMPLE ? 0 : (size_t)2 * (kp.n_max + 1) * R + 2)) +
-                        (MODE == KB_RESAMPLE ? 0 : sizeof(float2) * (size_t)FFT::TW_FLOAT2);
+                        (MODE == KB_RESAMPLE ? 0 : sizeof(float2) * ((size_t)FFT::TW_FLOAT2 + kp.n_max + 1));
     int dev = 0;
     cudaGetDevice(&dev);
     static size_t configured[64] = {0};

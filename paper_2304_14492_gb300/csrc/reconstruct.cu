@@ -91,7 +91,7 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // into one record part[b][blockIdx.x] (Eq. 10 / Eq. 13 on the polar nodes); `out`
 // may then be NULL.
 template <int LOGN, bool ERR>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho,
              float* __restrict__ out, const float* __restrict__ ref, double* __restrict__ part) {
     using FFT = RingFFT<LOGN>;
@@ -106,8 +106,10 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     const int b = blockIdx.y;
     const int i0 = blockIdx.x * R;
     const int nm1 = n_max + 1;
-    float2* twt = Gs + R * nm1;
+    float2* twt = Gs + R * nm1;                                   // warp-FFT twiddles
+    float2* twm = twt + FFT::TW_FLOAT2;                           // e^{-2 pi i m / N}, m < M
     FFT::load_twiddles(twt, tw);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) twm[m] = __ldg(&tw[m]);
     for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
         const int r = e % R, m = e / R;
         const int i = i0 + r;
@@ -129,7 +131,7 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
         if (m <= n_max) Sm = (m == 0) ? make_float2(2.f * Gr[0].x, 0.f) : Gr[m];
         const int q = M - m;
         if (q >= 1 && q <= n_max) T = cconj(Gr[q]);
-        const float2 w = __ldg(&tw[m]);                  // e^{-2 pi i m/N}
+        const float2 w = twm[m];                         // e^{-2 pi i m/N}
         const float2 ie = make_float2(w.y, w.x);         // i e^{+2 pi i m/N} = i conj(w)
         const float2 C = cadd(cadd(Sm, T), cmul(ie, csub(Sm, T)));
         v[a] = (lane < L) ? C : make_float2(0.f, 0.f);
@@ -142,18 +144,23 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
         float2* o = out ? reinterpret_cast<float2*>(out + row) : nullptr;
         if (ERR) {
             const float2* rf = reinterpret_cast<const float2*>(ref + row);
-            float2 f[Q];
+            // groups of four loads in flight, consumed as they arrive (few live registers)
 #pragma unroll
-            for (int r = 0; r < Q; ++r) f[r] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r)]);
+            for (int r0 = 0; r0 < Q; r0 += 4) {
+                float2 f[4];
 #pragma unroll
-            for (int r = 0; r < Q; ++r) {
-                const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
-                if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
-                const float d0 = f[r].x - x.x, d1 = f[r].y - x.y;
-                sd = fmaf(d0, d0, fmaf(d1, d1, sd));
-                sf = fmaf(f[r].x, f[r].x, fmaf(f[r].y, f[r].y, sf));
-                mx = fmaxf(mx, fmaxf(f[r].x, f[r].y));
-                cnt += 2.f;
+                for (int u = 0; u < 4 && r0 + u < Q; ++u) f[u] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r0 + u)]);
+#pragma unroll
+                for (int u = 0; u < 4 && r0 + u < Q; ++u) {
+                    const int r = r0 + u;
+                    const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
+                    if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
+                    const float d0 = f[u].x - x.x, d1 = f[u].y - x.y;
+                    sd = fmaf(d0, d0, fmaf(d1, d1, sd));
+                    sf = fmaf(f[u].x, f[u].x, fmaf(f[u].y, f[u].y, sf));
+                    mx = fmaxf(mx, fmaxf(f[u].x, f[u].y));
+                    cnt += 2.f;
+                }
             }
         } else {
 #pragma unroll
@@ -198,7 +205,7 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
                          const float* ref, double* part, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const int R = 8;
-    const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2);
+    const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2 + FFT::M);
     int dev = 0;
     cudaGetDevice(&dev);
     static size_t configured[64] = {0};
