@@ -201,6 +201,48 @@ int zm_project(zm_plan_t plan, const float* spectra, int batch, float* out,
 int zm_project_noalloc(zm_plan_t plan, const float* spectra, int batch, float* out,
                        unsigned flags, void* stream);
 
+/* ---- uneven batches ------------------------------------------------------ */
+
+/* One request of an uneven batch: an image with its own order and polar grid.
+ * out: device float[P(n_max)][2] (moment layout as zm_moments). */
+typedef struct {
+    zm_image_t image;
+    int n_max;
+    int n_rho, n_theta;      /* n_theta a power of two >= 2 n_max + 1 */
+    float* out;
+} zm_request_t;
+
+typedef struct zm_batch_s* zm_batch_t;
+
+/*
+ * Prepare an uneven batch: requests are grouped by (n_rho, n_theta); each group
+ * gets one plan whose n_max is the group's largest (a request's moments are the
+ * prefix P(n_max) of the group's, since Z_nm does not depend on the plan's
+ * order).  Workspaces are reserved, and for every group the launch choices
+ * (resampling by TMA tiles or by the fused gather kernel, rings per CTA of the
+ * ring FFT, radial split of the projection) are picked by timing candidates on
+ * the given images, or read from the JSON cache named by the environment
+ * variable ZM_TUNE_CACHE (which is then updated).  Synchronous; allocates.
+ *  plan_flags: one ZM_GRID_* | one ZM_PREC_*, for every group.
+ */
+int zm_batch_create(zm_batch_t* batch, const zm_request_t* reqs, int count, unsigned plan_flags);
+
+/*
+ * Moments of every request of the batch, enqueued on `stream` as one CUDA graph
+ * launch.  `reqs` must match the batch's requests in count, sizes, geometry,
+ * orders and grids; its image and output pointers may change, in which case
+ * the graph is captured again (synchronously) before it is launched.
+ *  flags: ZM_NEUMANN as zm_moments.
+ */
+int zm_batch_run(zm_batch_t batch, const zm_request_t* reqs, unsigned flags, void* stream);
+
+/* Number of groups (plans) of the batch and number of graph captures so far;
+ * either pointer may be NULL. */
+int zm_batch_info(zm_batch_t batch, int* groups, int* captures);
+
+/* Release the batch, its plans and graph (waits for the device). */
+int zm_batch_destroy(zm_batch_t batch);
+
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic counter; never reset). */
 unsigned long long zm_launch_count(void);

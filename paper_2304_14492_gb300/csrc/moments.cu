@@ -278,7 +278,7 @@ static int launch_projection_fp32(zm_plan_t p, const float* F, int batch, float*
     const int ncol = 2 * batch;
     const int ctiles = (ncol + KC_COLS - 1) / KC_COLS;
     const int base = (p->n_max + 1) * ctiles;
-    const int target = 4 * num_sms(p->device);
+    const int target = (p->tune_split > 0 ? p->tune_split : 4) * num_sms(p->device);
     const int kchunks = (p->n_rho + KC_K - 1) / KC_K;
     int S = std::max(1, std::min(kchunks, (target + base - 1) / base));
     const int chunk = ((kchunks + S - 1) / S) * KC_K;
@@ -299,6 +299,7 @@ static int launch_projection_fp32(zm_plan_t p, const float* F, int batch, float*
 
 // ============================================================== driver
 static int pick_rings(zm_plan_t p, int batch) {
+    if (p->tune_rings == 2 || p->tune_rings == 4 || p->tune_rings == 8) return p->tune_rings;
     int R = 8;
     const int want = 2 * num_sms(p->device);
     while (R > 2 && ((p->n_rho + R - 1) / R) * batch < want) R >>= 1;
@@ -361,8 +362,9 @@ static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int 
 int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* F,
                    float* fhat_out, bool resample_only, cudaStream_t st) {
     if (fhat_in) return launch_polar_fft(p, fhat_in, 0, batch, batch, F, st);
+    auto use_tma = [&](int b) { return !p->tune_gather && tma_eligible(imgs[b]); };
     bool any_tma = false;
-    for (int b = 0; b < batch && !any_tma; ++b) any_tma = tma_eligible(imgs[b]);
+    for (int b = 0; b < batch && !any_tma; ++b) any_tma = use_tma(b);
     float* fh = fhat_out;
     if (any_tma && !fh) {
         const int s = p->ws_fhat.grow(sizeof(float) * (size_t)batch * p->n_rho * p->n_theta);
@@ -373,12 +375,12 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
     while (b < batch) {
         int e = b + 1;
         int s;
-        if (tma_eligible(imgs[b])) {
-            while (e < batch && tma_eligible(imgs[e]) && same_geometry(imgs[b], imgs[e])) ++e;
+        if (use_tma(b)) {
+            while (e < batch && use_tma(e) && same_geometry(imgs[b], imgs[e])) ++e;
             s = launch_resample_tiles(p, imgs, b, e - b, fh, st);
             if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, st);
         } else {
-            while (e < batch && !tma_eligible(imgs[e])) ++e;
+            while (e < batch && !use_tma(e)) ++e;
             s = launch_gather(p, imgs, b, e - b, batch, F, fhat_out, resample_only, st);
         }
         if (s != ZM_OK) return s;
@@ -464,13 +466,18 @@ extern "C" int zm_plan_reserve(zm_plan_t plan, int batch) {
     if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
     if (batch < 1) return set_error(ZM_EINVAL, "batch must be >= 1");
     DeviceGuard g(plan->device);
-    int s = plan->ws_F.grow(sizeof(float) * (size_t)(plan->n_max + 1) * batch * 2 * plan->n_rho);
-    if (s != ZM_OK) return s;
-    // generous bound for the projection partials (S <= N_rho / 32 + 1)
-    const int S = std::min((plan->n_rho + KC_K - 1) / KC_K, 4 * num_sms(plan->device));
-    s = plan->ws_part.grow(sizeof(float) * (size_t)S * plan->P * 2 * batch);
-    if (s != ZM_OK) return s;
-    s = plan->ws_G.grow(sizeof(float) * (size_t)(plan->n_max + 1) * batch * 2 * plan->n_rho);
-    if (s != ZM_OK) return s;
-    return ZM_OK;
+    const size_t nb = (size_t)batch;
+    int s = plan->ws_F.grow(sizeof(float) * (size_t)(plan->n_max + 1) * nb * 2 * plan->n_rho);
+    // polar samples of the tile resampler
+    if (s == ZM_OK) s = plan->ws_fhat.grow(sizeof(float) * nb * plan->n_rho * plan->n_theta);
+    // projection partials: the radial split never exceeds one slice per 32 nodes
+    const size_t S = (size_t)(plan->n_rho + KC_K - 1) / KC_K;
+    if (s == ZM_OK) s = plan->ws_part.grow(sizeof(float) * S * plan->P * 2 * nb);
+    if (s == ZM_OK) s = plan->ws_colmax.grow(sizeof(unsigned) * 2 * nb);
+    if (s == ZM_OK) s = plan->ws_G.grow(sizeof(float) * (size_t)(plan->n_max + 1) * nb * 2 * plan->n_rho);
+    // reductions: 64 records per image (pixel errors) or one per 8 rings (fused errors)
+    const size_t rec = std::max<size_t>(64, (size_t)(plan->n_rho + 7) / 8);
+    if (s == ZM_OK) s = plan->ws_red.grow(sizeof(double) * nb * rec * 4);
+    if (s == ZM_OK) s = plan->ws_scale.grow(sizeof(float) * 2 * nb);
+    return s;
 }

@@ -353,7 +353,7 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
     const int base = (p->n_max + 1) * ctiles;
     // enough CTAs to cover the load -> MMA latency: up to one 64-wide chunk of
     // the radial index per CTA, at most 32 slices
-    const int target = 8 * num_sms_tc(p->device);
+    const int target = (p->tune_split > 0 ? p->tune_split : 8) * num_sms_tc(p->device);
     const int kchunks = (p->n_rho + TC_KC - 1) / TC_KC;
     int S = std::max(1, std::min(std::min(kchunks, 32), (target + base - 1) / base));
     const int chunk = ((kchunks + S - 1) / S) * TC_KC;

@@ -112,6 +112,10 @@ struct zm_plan_s {
     int* status = nullptr;      // device status word: ZM_ETIMEOUT after a timed-out wait
     // launch choices
     int kb_rings = 8;           // rings per CTA in the resample + FFT kernel
+    // set by the batch autotuner (0 = built-in heuristic)
+    int tune_gather = 0;        // 1: resample with the fused gather kernel even where TMA could stage
+    int tune_rings = 0;         // rings per CTA of the ring-FFT kernels (2, 4 or 8)
+    int tune_split = 0;         // CTAs per SM aimed at by the projection's radial split
 };
 
 namespace zm {

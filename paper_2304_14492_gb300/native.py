@@ -44,6 +44,10 @@ class zm_canvas_t(ctypes.Structure):
                 ("cx", c_float), ("cy", c_float), ("radius", c_float)]
 
 
+class zm_request_t(ctypes.Structure):
+    _fields_ = [("image", zm_image_t), ("n_max", c_int), ("n_rho", c_int), ("n_theta", c_int), ("out", c_void_p)]
+
+
 # name -> (restype, argtypes); mirrors include/zm.h
 SIGNATURES = {
     "zm_num_moments": (c_int, [c_int]),
@@ -65,6 +69,10 @@ SIGNATURES = {
     "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
     "zm_project": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_project_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_batch_create": (c_int, [POINTER(c_void_p), POINTER(zm_request_t), c_int, c_uint]),
+    "zm_batch_run": (c_int, [c_void_p, POINTER(zm_request_t), c_uint, c_void_p]),
+    "zm_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "zm_batch_destroy": (c_int, [c_void_p]),
     "zm_launch_count": (ctypes.c_ulonglong, []),
     "zm_reconstruct": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_reconstruct_errors": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_uint, c_void_p]),
@@ -235,6 +243,39 @@ def zm_project(plan, spectra, batch, out, flags=0, stream=None):
 
 def zm_project_noalloc(plan, spectra, batch, out, flags=0, stream=None):
     _check(lib().zm_project_noalloc(plan, _ptr(spectra), batch, _ptr(out), flags, _stream(stream)))
+
+
+def requests(items):
+    """zm_request_t array from (image tensor, n_max, n_rho, n_theta, out tensor[, geometry]) tuples."""
+    items = list(items)
+    arr = (zm_request_t * len(items))()
+    for j, it in enumerate(items):
+        img, n_max, n_rho, n_theta, out = it[:5]
+        geo = it[5] if len(it) > 5 else None
+        arr[j] = zm_request_t(image_desc(img, geo), n_max, n_rho, n_theta, _ptr(out))
+    return arr
+
+
+def zm_batch_create(reqs, plan_flags=0):
+    arr = reqs if isinstance(reqs, ctypes.Array) else requests(reqs)
+    h = c_void_p()
+    _check(lib().zm_batch_create(ctypes.byref(h), arr, len(arr), plan_flags))
+    return h.value
+
+
+def zm_batch_run(batch, reqs, flags=0, stream=None):
+    arr = reqs if isinstance(reqs, ctypes.Array) else requests(reqs)
+    _check(lib().zm_batch_run(batch, arr, flags, _stream(stream)))
+
+
+def zm_batch_info(batch):
+    g, c = c_int(), c_int()
+    _check(lib().zm_batch_info(batch, ctypes.byref(g), ctypes.byref(c)))
+    return {"groups": g.value, "captures": c.value}
+
+
+def zm_batch_destroy(batch):
+    _check(lib().zm_batch_destroy(batch))
 
 
 def zm_launch_count():
