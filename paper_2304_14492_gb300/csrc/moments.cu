@@ -127,11 +127,11 @@ __global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ Kb
                 v[s] = (lane < FFT::L) ? z[lane + FFT::L * s] : make_float2(0.f, 0.f);
             __syncwarp();
         }
-        FFT::forward(v, lane, twt);
         float2* X = reinterpret_cast<float2*>(row);
+        FFT::fwd(v, lane, twt, X);                 // the row doubles as the transpose buffer
         if (lane < FFT::L) {
 #pragma unroll
-            for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::out_index(r, lane))] = v[r];
+            for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::fwd_index(r, lane))] = v[r];
         }
         __syncwarp();
         for (int m = lane; m <= n_max; m += 32) {

@@ -91,7 +91,7 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // into one record part[b][blockIdx.x] (Eq. 10 / Eq. 13 on the polar nodes); `out`
 // may then be NULL.
 template <int LOGN, bool ERR>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4))
 k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho,
              float* __restrict__ out, const float* __restrict__ ref, double* __restrict__ part) {
     using FFT = RingFFT<LOGN>;
@@ -108,6 +108,7 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     const int nm1 = n_max + 1;
     float2* twt = Gs + R * nm1;                                   // warp-FFT twiddles
     float2* twm = twt + FFT::TW_FLOAT2;                           // e^{-2 pi i m / N}, m < M
+    float2* tbuf = twm + M + warp * FFT::TBUF;                    // per-warp transpose buffer
     FFT::load_twiddles(twt, tw);
     for (int m = threadIdx.x; m < M; m += blockDim.x) twm[m] = __ldg(&tw[m]);
     for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
@@ -122,11 +123,10 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     }
     __syncthreads();
     const float2* Gr = Gs + warp * nm1;
-    const int cidx = FFT::brev_lane(lane & (L - 1));
     float2 v[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        const int m = a + Q * cidx;
+        const int m = FFT::inv_index(a, lane);
         float2 Sm = make_float2(0.f, 0.f), T = make_float2(0.f, 0.f);
         if (m <= n_max) Sm = (m == 0) ? make_float2(2.f * Gr[0].x, 0.f) : Gr[m];
         const int q = M - m;
@@ -136,7 +136,7 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
         const float2 C = cadd(cadd(Sm, T), cmul(ie, csub(Sm, T)));
         v[a] = (lane < L) ? C : make_float2(0.f, 0.f);
     }
-    FFT::inverse_natural(v, lane, twt);
+    FFT::inv(v, lane, twt, tbuf);
     const int i = i0 + warp;
     float sd = 0.f, sf = 0.f, mx = -INFINITY, cnt = 0.f;
     if (i < n_rho && lane < L) {
@@ -205,7 +205,7 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
                          const float* ref, double* part, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const int R = 8;
-    const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2 + FFT::M);
+    const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2 + FFT::M + (size_t)R * FFT::TBUF);
     int dev = 0;
     cudaGetDevice(&dev);
     static size_t configured[64] = {0};

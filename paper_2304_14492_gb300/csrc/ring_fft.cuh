@@ -52,13 +52,50 @@ struct RingFFT {
     //   t2[k1 * L + t] = W_M^{t k1},          k1 < Q    (between the stages)
     //   t3[e * L + t]  = W_{2h}^{t mod h},    h = 2^e   (cross-lane stages)
     // with W_n = e^{-2 pi i / n}; the inverse uses their conjugates.
+    //   t32[x]         = W_32^x,             x < 32    (transposed form only)
     static constexpr int TW_T1 = Q / 2 > 0 ? Q / 2 : 1;
-    static constexpr int TW_FLOAT2 = TW_T1 + Q * L + (LOGL > 0 ? LOGL : 1) * L;
+    static constexpr int TW_T3 = (LOGL > 0 ? LOGL : 1) * L;
+    static constexpr int TW_FLOAT2 = TW_T1 + Q * L + TW_T3 + 32;
+
+    // Transposed form (Q >= 4, i.e. N >= 256): the 32-point DFTs across lanes
+    // are done by G = 32/Q lanes each, so only log2(G) shuffle stages remain;
+    // a per-warp shared buffer of TBUF float2 (rows of 33) carries the transpose.
+    static constexpr bool TRANSPOSED = LOGQ >= 2;
+    static constexpr int LOGG = TRANSPOSED ? 5 - LOGQ : 0;
+    static constexpr int G = 1 << LOGG;
+    static constexpr int TSTRIDE = 33;
+    static constexpr int TBUF = TRANSPOSED ? Q * TSTRIDE : 0;
+
+    // In-register Q-point DFT (decimation in frequency): v[r] becomes the
+    // transform at index brev_Q(r); INV uses e^{+2 pi i / Q}.
+    template <bool INV>
+    __device__ static __forceinline__ void reg_dft(float2 (&v)[Q], const float2* t1) {
+#pragma unroll
+        for (int h = Q / 2; h >= 1; h >>= 1) {
+#pragma unroll
+            for (int b = 0; b < Q; b += 2 * h) {
+#pragma unroll
+                for (int j = 0; j < h; ++j) {
+                    const float2 x = v[b + j], y = v[b + j + h];
+                    v[b + j] = cadd(x, y);
+                    const float2 d = csub(x, y);
+                    if (j == 0) {
+                        v[b + j + h] = d;
+                    } else {
+                        const float2 w = t1[j * (Q / (2 * h))];
+                        v[b + j + h] = cmul(d, INV ? cconj(w) : w);
+                    }
+                }
+            }
+        }
+    }
 
     __device__ static __forceinline__ void load_twiddles(float2* tab, const float2* __restrict__ tw) {
         float2* t1 = tab;
         float2* t2 = tab + TW_T1;
         float2* t3 = t2 + Q * L;
+        float2* t32 = t3 + TW_T3;
+        for (int x = threadIdx.x; x < 32; x += blockDim.x) t32[x] = N >= 32 ? __ldg(&tw[x * (N >= 32 ? N / 32 : 1)]) : make_float2(1.f, 0.f);
         for (int x = threadIdx.x; x < Q / 2; x += blockDim.x) t1[x] = __ldg(&tw[x * (N / Q)]);
         for (int e = threadIdx.x; e < Q * L; e += blockDim.x) {
             const int k1 = e / L, t = e - k1 * L;
@@ -152,6 +189,111 @@ struct RingFFT {
                     v[b + j + h] = (j == 0) ? d : cmul(d, cconj(t1[j * (Q / (2 * h))]));
                 }
             }
+        }
+    }
+
+    __device__ static __forceinline__ int brev_g(int g) {
+        return LOGG == 0 ? 0 : (int)(__brev((unsigned)g) >> (32 - LOGG));
+    }
+
+    // Transposed forward DFT.  In: lane t, register s = z[t + 32 s].  With
+    // k = k1 + Q (a + Q b):  A) Q-point DFT over s, B) twiddle W_M^{t k1},
+    // transpose so that lane (k1, g) (k1 = lane / G, g = lane mod G) holds
+    // Y[k1][g + G u], u < Q;  C1) Q-point DFT over u, C2) twiddle W_32^{g a},
+    // C3) G-point DFT across the group's lanes.  Out: see fwd_index().
+    __device__ static __forceinline__ void forward_t(float2 (&v)[Q], int lane, const float2* tab, float2* buf) {
+        const float2* t1 = tab;
+        const float2* t2 = tab + TW_T1;
+        const float2* t32 = t2 + Q * L + TW_T3;
+        reg_dft<false>(v, t1);
+#pragma unroll
+        for (int r = 1; r < Q; ++r) v[r] = cmul(v[r], t2[brev_c<LOGQ>(r) * L + lane]);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < Q; ++r) buf[brev_c<LOGQ>(r) * TSTRIDE + lane] = v[r];
+        __syncwarp();
+        const int k1 = lane >> LOGG, g = lane & (G - 1);
+#pragma unroll
+        for (int u = 0; u < Q; ++u) v[u] = buf[k1 * TSTRIDE + g + G * u];
+        __syncwarp();
+        reg_dft<false>(v, t1);
+#pragma unroll
+        for (int r = 1; r < Q; ++r) v[r] = cmul(v[r], t32[g * brev_c<LOGQ>(r)]);
+#pragma unroll
+        for (int h = G / 2; h >= 1; h >>= 1) {
+            const bool upper = (g & h) != 0;
+            const float2 w = t32[(g & (h - 1)) * (16 / h)];
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                float2 p;
+                p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
+                p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
+                v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
+            }
+        }
+    }
+
+    // Transposed inverse DFT z_j = sum_m C_m e^{+2 pi i j m / M}.  In: lane
+    // (k1, g), register a = C[k1 + Q (a + Q brev_G(g))] (see inv_index()).
+    // Out: lane t, register r = z[t + 32 brev_Q(r)] (natural across lanes).
+    __device__ static __forceinline__ void inverse_t(float2 (&v)[Q], int lane, const float2* tab, float2* buf) {
+        const float2* t1 = tab;
+        const float2* t2 = tab + TW_T1;
+        const float2* t32 = t2 + Q * L + TW_T3;
+        const int k1 = lane >> LOGG, g = lane & (G - 1);
+#pragma unroll
+        for (int lg = 0; lg < LOGG; ++lg) {
+            const int h = 1 << lg;
+            const bool upper = (g & h) != 0;
+            const float2 w = cconj(t32[(g & (h - 1)) * (16 / h)]);
+#pragma unroll
+            for (int r = 0; r < Q; ++r) {
+                float2 p;
+                p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
+                p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
+                v[r] = upper ? csub(p, cmul(w, v[r])) : cadd(v[r], cmul(w, p));
+            }
+        }
+#pragma unroll
+        for (int a = 1; a < Q; ++a) v[a] = cmul(v[a], cconj(t32[g * a]));
+        reg_dft<true>(v, t1);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < Q; ++r) buf[k1 * TSTRIDE + g + G * brev_c<LOGQ>(r)] = v[r];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < Q; ++q) v[q] = buf[q * TSTRIDE + lane];
+        __syncwarp();
+#pragma unroll
+        for (int q = 1; q < Q; ++q) v[q] = cmul(v[q], cconj(t2[q * L + lane]));
+        reg_dft<true>(v, t1);
+    }
+
+    // Whichever form fits N: forward / inverse with their index maps.
+    __device__ static __forceinline__ void fwd(float2 (&v)[Q], int lane, const float2* tab, float2* buf) {
+        if constexpr (TRANSPOSED) forward_t(v, lane, tab, buf);
+        else forward(v, lane, tab);
+    }
+    __device__ static __forceinline__ void inv(float2 (&v)[Q], int lane, const float2* tab, float2* buf) {
+        if constexpr (TRANSPOSED) inverse_t(v, lane, tab, buf);
+        else inverse_natural(v, lane, tab);
+    }
+    // index of the spectrum held in register r of `lane` after fwd()
+    __device__ static __forceinline__ int fwd_index(int r, int lane) {
+        if constexpr (TRANSPOSED) {
+            const int k1 = lane >> LOGG, g = lane & (G - 1);
+            return k1 + Q * (brev_c<LOGQ>(r) + Q * brev_g(g));
+        } else {
+            return out_index(r, lane);
+        }
+    }
+    // index of the spectrum inv() expects in register a of `lane`
+    __device__ static __forceinline__ int inv_index(int a, int lane) {
+        if constexpr (TRANSPOSED) {
+            const int k1 = lane >> LOGG, g = lane & (G - 1);
+            return k1 + Q * (a + Q * brev_g(g));
+        } else {
+            return a + Q * brev_lane(lane & (L - 1));
         }
     }
 
