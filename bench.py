@@ -192,21 +192,25 @@ def blas_threads():
     return os.cpu_count()
 
 
-def cpu_baseline(budget_s=12.0):
-    """Whole frames through the oracle on the host cores for about budget_s."""
-    img = make_frames(1, start=1000)[0].astype(np.float64)
+def cpu_baseline(img, budget_s=12.0):
+    """Whole frames (the frame `img`, repeated) through the oracle on the host
+    cores for about budget_s.  Returns the line's cpu_baseline object and the
+    oracle's moments of `img`."""
     rings = np.arange(N_RHO)
     t0 = time.perf_counter()
     n = 0
+    Zref = None
     while True:
-        oracle_pass(img, rings)
+        Z, _ = oracle_pass(img, rings)
+        if Zref is None:
+            Zref = Z
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 64:
             break
     return {"value": n / el, "unit": "images/s", "cores": blas_threads(), "kind": "oracle",
             "sample": "%d whole 4K frame(s) through the FP64 oracle (moments + polar reconstruction + errors), "
-                      "%.1f s of CPU time, numpy/BLAS on %d host cores" % (n, el, os.cpu_count())}
+                      "%.1f s of CPU time, numpy/BLAS on %d host cores" % (n, el, os.cpu_count())}, Zref
 
 
 def run_reference(args):
@@ -371,7 +375,13 @@ def run_gb300(args):
 
     if rank == 0 and not args.quick:
         line.update(extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P))
-        line["cpu_baseline"] = cpu_baseline()
+        del views, imgs
+        torch.cuda.empty_cache()
+        img0, frame0 = line.pop("_frame0")
+        line["uneven_batch"] = bench_uneven(zm, torch, dev)
+        line["serving"] = bench_serving(zm)
+        line["cpu_baseline"], Zref = cpu_baseline(img0)
+        line["err_vs_fp64"] = {k: float(np.max(np.abs(z - Zref)) / np.max(np.abs(Zref))) for k, z in frame0.items()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -399,18 +409,16 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
     if plan32 != plan:
         res["moments_only_images_per_s"]["fp32"] = moments_rate(plan32)
 
-    # error vs the FP64 oracle for every precision, on frame 0
-    import oracle
-    img0 = views[0].double().cpu().numpy()
-    Zref = oracle.moments.moments(img0, N_MAX, N_RHO, N_THETA)
-    errs = {}
+    # frame 0 through every precision; compared with the FP64 oracle's moments
+    # of the same frame, which the cpu_baseline leg computes while it is timed
+    frame0 = {}
     for name, p in ((prec, plan), ("fp32", plan32)):
         o1 = torch.empty((1, P, 2), device=dev)
         zm.zm_moments(p, [views[0]], o1, 0, st)
         torch.cuda.synchronize(dev)
         z = o1[0].double().cpu().numpy()
-        errs[name] = oracle.metrics.rel_max_err(z[:, 0] + 1j * z[:, 1], Zref)
-    res["err_vs_fp64"] = errs
+        frame0[name] = z[:, 0] + 1j * z[:, 1]
+    res["_frame0"] = (views[0].double().cpu().numpy(), frame0)
 
     # single-frame latency (L2 flushed between calls)
     flush = torch.empty(64 * 2**20, device=dev, dtype=torch.float32)     # 256 MB > L2
@@ -463,6 +471,103 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
                   "h2d_bytes_per_step": B * H * W * 4, "d2h_bytes_per_step": B * P * 8 + B * 4 * 8,
                   "steps": reps}
     return res
+
+
+def bench_uneven(zm, torch, dev, count=256):
+    """Uneven batch (sizes 128..1024, n_max 30..80, N_rho = size/2): one graph
+    launch per replay; images/s per projection precision."""
+    from paper_2304_14492_gb300 import synth
+    specs = synth.uneven_batch_specs(count=count, workload=3)
+    pool = {}
+    items = []
+    for j, (size, n_max, n_rho, n_theta) in enumerate(specs):
+        key = (size, j % 4)
+        if key not in pool:
+            pool[key] = torch.from_numpy(synth.blob_image(size, size, 8, workload=3, index=j)).to(dev)
+        out = torch.empty((zm.zm_num_moments(n_max), 2), device=dev)
+        items.append((pool[key], n_max, n_rho, n_theta, out))
+    res = {"requests": count, "note": "4 distinct frames per size, each request its own output"}
+    st = torch.cuda.current_stream(dev)
+    for name, flag in (("bf16x3", zm.ZM_PREC_BF16X3), ("fp16x3", zm.ZM_PREC_FP16X3), ("fp32", zm.ZM_PREC_FP32)):
+        b = zm.zm_batch_create(items, flag)
+        try:
+            for _ in range(3):
+                zm.zm_batch_run(b, items, 0, st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record(st)
+            for _ in range(reps):
+                zm.zm_batch_run(b, items, 0, st)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            res[name] = {"images_per_s": count * reps / (e0.elapsed_time(e1) / 1000.0),
+                         "groups": zm.zm_batch_info(b)["groups"]}
+        finally:
+            zm.zm_batch_destroy(b)
+    return res
+
+
+def bench_serving(zm, rate=2000.0, seconds=10.0, seed=7):
+    """Poisson arrivals of host images (sizes 256/512/1024/2160-crop, n_max
+    20/50/100/200, N_rho = size/2, N_theta = next power of two >= 2 n_max + 2)
+    into the continuous-batching server; latency submit -> result on the host."""
+    from paper_2304_14492_gb300 import synth
+    rng = np.random.default_rng(seed)
+    sizes, orders = [256, 512, 1024, 2160], [20, 50, 100, 200]
+    pool = {}
+    for sz in sizes:
+        if sz == 2160:
+            frames = [synth.blob_image(H, W, N_BLOBS, workload=5, index=k) for k in range(2)]
+            pool[sz] = [np.ascontiguousarray(f[:, (W - H) // 2:(W - H) // 2 + H]) for f in frames]
+        else:
+            pool[sz] = [synth.blob_image(sz, sz, 8, workload=5, index=k) for k in range(4)]
+    n = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+    reqs = []
+    for j in range(n):
+        sz = int(rng.choice(sizes))
+        nm = int(rng.choice(orders))
+        nt = 1
+        while nt < 2 * nm + 2:
+            nt *= 2
+        img = pool[sz][j % len(pool[sz])]
+        reqs.append((img, nm, sz // 2, nt, np.empty((zm.zm_num_moments(nm), 2), np.float32)))
+    srv = zm.zm_server_create(4 << 30, 4, 64, zm.ZM_PREC_BF16X3)
+    try:
+        # resident plans for every grid first (plan builds are not request latency)
+        warm = [(sz, nm, np.empty((zm.zm_num_moments(nm), 2), np.float32)) for sz in sizes for nm in orders]
+        for sz, nm, o in warm:                 # the outputs stay referenced until drained
+            zm.zm_server_submit(srv, pool[sz][0], nm, sz // 2, 1 << max(3, (2 * nm + 1).bit_length()), o)
+        zm.zm_server_drain(srv, 120.0)
+        zm.zm_server_reset_stats(srv)
+        t0 = time.perf_counter()
+        for (img, nm, nr, nt, out), ta in zip(reqs, arrivals):
+            while time.perf_counter() - t0 < ta:
+                pass
+            zm.zm_server_submit(srv, img, nm, nr, nt, out)
+        zm.zm_server_drain(srv, 120.0)
+        wall = time.perf_counter() - t0
+        stats = zm.zm_server_stats(srv)
+        # every request again, alone (submit, wait), against its result in the mix
+        worst, rerun, t1 = 0.0, 0, time.perf_counter()
+        for img, nm, nr, nt, out in reqs:
+            if time.perf_counter() - t1 > 60.0:
+                break
+            o = np.empty_like(out)
+            zm.zm_server_wait(srv, zm.zm_server_submit(srv, img, nm, nr, nt, o), 30.0)
+            d = float(np.max(np.abs(o - out)) / max(float(np.max(np.abs(o))), 1e-30))
+            worst = max(worst, d)
+            rerun += 1
+    finally:
+        zm.zm_server_destroy(srv, 60.0)
+    del warm
+    done = stats["completed"]
+    return {"arrival_rate_per_s": rate, "requests": n, "completed": int(done), "wall_s": wall,
+            "images_per_s": done / wall, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+            "max_ms": stats["max_ms"], "groups_launched": int(stats["groups_launched"]),
+            "peak_device_bytes": int(stats["peak_bytes"]), "precision": "bf16x3",
+            "alone_vs_mix": {"requests_rerun": rerun, "max_rel_diff": worst},
+            "note": "statistics reset after 16 plan-warming requests; latency = submit -> moments in host memory"}
 
 
 def main():

@@ -243,6 +243,72 @@ int zm_batch_info(zm_batch_t batch, int* groups, int* captures);
 /* Release the batch, its plans and graph (waits for the device). */
 int zm_batch_destroy(zm_batch_t batch);
 
+/* ---- serving (continuous batching) ---------------------------------------- */
+
+typedef struct zm_server_s* zm_server_t;
+
+typedef struct {
+    unsigned long long hbm_budget;  /* bytes of device memory for requests in flight
+                                       (images and moments); 0 = 1 GiB */
+    int streams;                    /* CUDA streams work overlaps on; 0 = 4 */
+    int max_group;                  /* most requests launched together per grid; 0 = 64 */
+    unsigned plan_flags;            /* ZM_GRID_* | ZM_PREC_* of every plan */
+    int max_wait_us;                /* batching window: an admitted request waits at
+                                       most this long for others of its grid before
+                                       its group launches, unless the group is full
+                                       or the budget is exhausted; 0 = launch as soon
+                                       as the grid's stream has room */
+} zm_server_config_t;
+
+typedef struct {
+    unsigned long long submitted, completed, rejected;
+    unsigned long long groups_launched;
+    double p50_ms, p99_ms, max_ms;  /* latency: submit -> result on the host */
+    double images_per_s;            /* completed / (last completion - first submit) */
+    unsigned long long peak_bytes;  /* largest device footprint of requests in flight */
+} zm_server_stats_t;
+
+/*
+ * A server that computes moments of host images as requests arrive.  A
+ * scheduler thread admits waiting requests while their device bytes fit the
+ * budget (the arena is allocated once, here), groups the admitted ones by
+ * polar grid (one plan per (n_rho, n_theta), order = the largest seen), and
+ * launches each group on the stream bound to its grid: copy in, resampling,
+ * ring FFT, projection, copy out.  Groups of different grids overlap on the
+ * device; requests arriving meanwhile are admitted as memory frees up.
+ * Plans (tables on the device) stay resident for the server's lifetime.
+ */
+int zm_server_create(zm_server_t* server, const zm_server_config_t* config);
+
+/*
+ * Queue one request.  `image` (host, row pitch in elements) and `out` (host
+ * float[P(n_max)][2]) must stay valid until the request completes.  Returns a
+ * ticket in *ticket.  ZM_EINVAL for bad arguments; ZM_ENOMEM if the request
+ * alone exceeds the budget.  Geometry: the inscribed, centred disk.
+ */
+int zm_server_submit(zm_server_t server, const float* image, int height, int width, long long pitch,
+                     int n_max, int n_rho, int n_theta, float* out, unsigned flags,
+                     unsigned long long* ticket);
+
+/* 1 in *done if the ticket's result is in its `out`, else 0. */
+int zm_server_poll(zm_server_t server, unsigned long long ticket, int* done);
+
+/* Wait for a ticket at most timeout_s seconds: ZM_OK or ZM_ETIMEOUT. */
+int zm_server_wait(zm_server_t server, unsigned long long ticket, double timeout_s);
+
+/* Wait (at most timeout_s) until every submitted request has completed. */
+int zm_server_drain(zm_server_t server, double timeout_s);
+
+int zm_server_stats(zm_server_t server, zm_server_stats_t* stats);
+
+/* Zero every counter and latency sample (e.g. after warm-up requests that
+ * built the plans).  Only on a drained server: ZM_EINVAL while requests are
+ * in flight. */
+int zm_server_reset_stats(zm_server_t server);
+
+/* Stop the scheduler (after draining at most timeout_s) and free everything. */
+int zm_server_destroy(zm_server_t server, double timeout_s);
+
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic counter; never reset). */
 unsigned long long zm_launch_count(void);

@@ -62,7 +62,7 @@ __device__ __forceinline__ float bilinear(const GeoImage& im, float X, float Y) 
 //   F_m = (Z_m + conj Z_{M-m})/2 + e^{-2 pi i m/N} (Z_m - conj Z_{M-m})/(2i),
 // for m = 0..n_max.  Phase 3: F[m][b][re/im][i0..i0+R) written as segments.
 template <int LOGN, int MODE>
-__global__ void __launch_bounds__(512) k_ring_spectra(const __grid_constant__ KbParams p) {
+__global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(const __grid_constant__ KbParams p) {
     using FFT = RingFFT<LOGN>;
     constexpr int N = FFT::N;
     constexpr int ROW = FFT::ROW_FLOATS;

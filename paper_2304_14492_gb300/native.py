@@ -48,6 +48,18 @@ class zm_request_t(ctypes.Structure):
     _fields_ = [("image", zm_image_t), ("n_max", c_int), ("n_rho", c_int), ("n_theta", c_int), ("out", c_void_p)]
 
 
+class zm_server_config_t(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_ulonglong), ("streams", c_int), ("max_group", c_int), ("plan_flags", c_uint),
+                ("max_wait_us", c_int)]
+
+
+class zm_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
+                ("rejected", ctypes.c_ulonglong), ("groups_launched", ctypes.c_ulonglong),
+                ("p50_ms", c_double), ("p99_ms", c_double), ("max_ms", c_double),
+                ("images_per_s", c_double), ("peak_bytes", ctypes.c_ulonglong)]
+
+
 # name -> (restype, argtypes); mirrors include/zm.h
 SIGNATURES = {
     "zm_num_moments": (c_int, [c_int]),
@@ -73,6 +85,15 @@ SIGNATURES = {
     "zm_batch_run": (c_int, [c_void_p, POINTER(zm_request_t), c_uint, c_void_p]),
     "zm_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     "zm_batch_destroy": (c_int, [c_void_p]),
+    "zm_server_create": (c_int, [POINTER(c_void_p), POINTER(zm_server_config_t)]),
+    "zm_server_submit": (c_int, [c_void_p, c_void_p, c_int, c_int, c_longlong, c_int, c_int, c_int, c_void_p, c_uint,
+                                 POINTER(ctypes.c_ulonglong)]),
+    "zm_server_poll": (c_int, [c_void_p, ctypes.c_ulonglong, POINTER(c_int)]),
+    "zm_server_wait": (c_int, [c_void_p, ctypes.c_ulonglong, c_double]),
+    "zm_server_drain": (c_int, [c_void_p, c_double]),
+    "zm_server_stats": (c_int, [c_void_p, POINTER(zm_server_stats_t)]),
+    "zm_server_reset_stats": (c_int, [c_void_p]),
+    "zm_server_destroy": (c_int, [c_void_p, c_double]),
     "zm_launch_count": (ctypes.c_ulonglong, []),
     "zm_reconstruct": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_reconstruct_errors": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_uint, c_void_p]),
@@ -276,6 +297,55 @@ def zm_batch_info(batch):
 
 def zm_batch_destroy(batch):
     _check(lib().zm_batch_destroy(batch))
+
+
+def zm_server_create(hbm_budget=0, streams=0, max_group=0, plan_flags=0, max_wait_us=0):
+    cfg = zm_server_config_t(hbm_budget, streams, max_group, plan_flags, max_wait_us)
+    h = c_void_p()
+    _check(lib().zm_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+    return h.value
+
+
+def zm_server_submit(server, image, n_max, n_rho, n_theta, out, flags=0):
+    """image: C-contiguous float32 numpy array (host); out: float32 numpy array of
+    shape [P(n_max), 2].  Both must stay alive until the ticket completes."""
+    import numpy as np
+    if image.dtype != np.float32 or image.ndim != 2 or not image.flags.c_contiguous:
+        raise ValueError("image must be a C-contiguous 2-D float32 array")
+    if out.dtype != np.float32 or not out.flags.c_contiguous or out.size < 2 * zm_num_moments(n_max):
+        raise ValueError("out must be a C-contiguous float32 array of P(n_max) x 2")
+    t = ctypes.c_ulonglong()
+    _check(lib().zm_server_submit(server, image.ctypes.data, image.shape[0], image.shape[1], image.shape[1],
+                                  n_max, n_rho, n_theta, out.ctypes.data, flags, ctypes.byref(t)))
+    return t.value
+
+
+def zm_server_poll(server, ticket):
+    d = c_int()
+    _check(lib().zm_server_poll(server, ticket, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def zm_server_wait(server, ticket, timeout_s=10.0):
+    _check(lib().zm_server_wait(server, ticket, timeout_s))
+
+
+def zm_server_drain(server, timeout_s=60.0):
+    _check(lib().zm_server_drain(server, timeout_s))
+
+
+def zm_server_stats(server):
+    st = zm_server_stats_t()
+    _check(lib().zm_server_stats(server, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in zm_server_stats_t._fields_}
+
+
+def zm_server_reset_stats(server):
+    _check(lib().zm_server_reset_stats(server))
+
+
+def zm_server_destroy(server, timeout_s=60.0):
+    _check(lib().zm_server_destroy(server, timeout_s))
 
 
 def zm_launch_count():
