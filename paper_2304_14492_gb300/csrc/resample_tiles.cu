@@ -7,11 +7,18 @@
 // Which samples a tile owns depends only on the geometry, so k_tile_plan
 // decides it once per geometry (from the candidates' anchors, computed with the
 // same float arithmetic as every later pass, so the tiles partition the samples
-// exactly) and stores them as packed (ring, angle) indices.  Per frame, a CTA
-// loads its tile and a one-pixel halo (a 68x65 box, zero outside the image) with
-// one TMA copy and interpolates exactly its own samples from shared memory into
-// f_hat[b][i][k].  Each image pixel is read from HBM once and every gather is a
-// shared-memory access.
+// exactly) and k_tile_records turns each into a 16-byte record: the stencil's
+// offset in the tile box, the output offset and the two bilinear fractions.
+// Per frame, a CTA starts one TMA copy of its tile and a one-pixel halo (a
+// 68x65 box, zero outside the image), loads its records while the box is in
+// flight, and interpolates exactly its own samples from shared memory into
+// f_hat[b][i][k].  Each image pixel is read from HBM about once, every gather
+// is a shared-memory access, and a CTA's critical path holds two dependent
+// global loads (its item, then its records) besides the box.
+//
+// The ZM_TILE_* macros fix the tile shape and the launch shape; the defaults
+// are the fastest of a sweep on GB300 at 4K (64x64 tiles, four samples per
+// thread in flight, eight CTAs per SM, one image per CTA).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -27,37 +34,62 @@
 
 namespace zm {
 
-constexpr int TILE = 64;                 // anchors per tile side
-constexpr int BOX_W = TILE + 4;          // 16-byte multiple, covers x_t .. x_t + 64
-constexpr int BOX_H = TILE + 1;          // covers y_t .. y_t + 64
+#ifndef ZM_TILE_W
+#define ZM_TILE_W 64
+#endif
+#ifndef ZM_TILE_H
+#define ZM_TILE_H 64
+#endif
+constexpr int TILE_W = ZM_TILE_W;        // anchors per tile row (a multiple of 4)
+constexpr int TILE_H = ZM_TILE_H;        // anchor rows per tile
+constexpr int BOX_W = TILE_W + 4;        // 16-byte multiple, covers x_t .. x_t + TILE_W
+constexpr int BOX_H = TILE_H + 1;        // covers y_t .. y_t + TILE_H
 constexpr int TILE_X0 = -4;              // x_t = -4 + 64 tx (multiple of 4, as TMA needs)
 constexpr int TILE_Y0 = -1;              // y_t = -1 + 64 ty
 constexpr int TILE_MAXC = 8192;          // candidates per work item
 constexpr int TILE_MAXR = 1024;          // rings per work item
 constexpr int TILE_MAX_IMG = 64;         // tensor maps per launch
 constexpr int TILE_THREADS = 256;
+#ifndef ZM_TILE_G
+#define ZM_TILE_G 4
+#endif
+#ifndef ZM_TILE_MINB
+#define ZM_TILE_MINB 8
+#endif
+#ifndef ZM_TILE_IPC
+#define ZM_TILE_IPC 1
+#endif
+constexpr int TILE_IPC = ZM_TILE_IPC;    // images per CTA (boxes in flight per CTA)
+constexpr int TILE_BOX_FLOATS = ((BOX_H * BOX_W + 31) / 32) * 32;   // 128-byte aligned boxes
+constexpr int TILE_G = ZM_TILE_G;        // samples per thread handled together
+constexpr int TILE_MINB = ZM_TILE_MINB;  // resident CTAs per SM the registers allow
 constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;
 
-struct TileItem {
+struct __align__(16) TileItem {
     int x_t, y_t;        // anchor origin of the tile
     int i_lo, i_hi;      // rings [i_lo, i_hi)
     int k_lo, k_n;       // angles (k_lo + j) mod N, j < k_n; k_lo in [0, N)
+    int s0, cnt;         // the item's samples: [s0, s0 + cnt) of the plan's list
 };
 
 // Packed sample of a work item: (ring offset << 11) | angle offset in the
 // item's staged angle window (ring offset < 1024, angle offset < 2048).
 constexpr int SAMPLE_KBITS = 11;
 
+// A planned sample, ready to interpolate: shared-memory offset of its 2x2
+// stencil in the box, output offset in the item's ring block, and the bilinear
+// fractions (as float bits).
+struct TileRecord {
+    int so, oo, fx, fy;
+};
+
 struct TileParams {
     const TileItem* items;
-    const uint32_t* samples;     // packed samples of all items
-    const int* item_off;         // [n_items + 1] first sample of each item
-    const float* rho32;
-    const float2* cs;
+    const int4* recs;            // TileRecord of every planned sample, item after item
     float* fhat;
     int* status;
     int n_rho, N, b_off;
-    float cx, cy, r;
+    int nb;                      // images in this launch
     CUtensorMap maps[TILE_MAX_IMG];
 };
 
@@ -75,14 +107,14 @@ __device__ __forceinline__ void sample_xy(float rad, float2 cv, float cx, float 
 
 // Planning pass over the candidate (ring, angle) pairs of each item: keeps
 // those whose anchor lies in the item's tile.  count_only: counts[item];
-// otherwise writes the packed samples in candidate order from item_off[item].
+// otherwise writes the packed samples in candidate order from items[item].s0.
 struct PlanParams {
     const TileItem* items;
     const float* rho32;
     const float2* cs;
     int* counts;
-    const int* item_off;
     uint32_t* samples;
+    int4* recs;
     int N;
     float cx, cy, r;
     int count_only;
@@ -98,7 +130,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_plan(const __grid_constan
     const float xt = (float)it.x_t, yt = (float)it.y_t;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int mine = 0;
-    if (threadIdx.x == 0) base_s = p.count_only ? 0 : p.item_off[blockIdx.x];
+    if (threadIdx.x == 0) base_s = p.count_only ? 0 : it.s0;
     __syncthreads();
     for (int c0 = 0; c0 < total; c0 += TILE_THREADS) {
         const int c = c0 + threadIdx.x;
@@ -112,7 +144,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_plan(const __grid_constan
             float X, Y;
             sample_xy(rad, cv, p.cx, p.cy, &X, &Y);
             const int lx = (int)(floorf(X) - xt), ly = (int)(floorf(Y) - yt);
-            valid = (unsigned)lx < (unsigned)TILE && (unsigned)ly < (unsigned)TILE;
+            valid = (unsigned)lx < (unsigned)TILE_W && (unsigned)ly < (unsigned)TILE_H;
         }
         if (p.count_only) {
             mine += valid ? 1 : 0;
@@ -146,86 +178,130 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_plan(const __grid_constan
     }
 }
 
-// Dynamic shared memory: the tile box, then the item's ring radii (<= TILE_MAXR)
-// and angle table (<= N entries).
-__global__ void __launch_bounds__(TILE_THREADS) k_resample_tiles(const __grid_constant__ TileParams p) {
-    extern __shared__ __align__(128) float tsm[];
-    float* tile = tsm;                                            // [BOX_H][BOX_W]
-    float* rad_s = tsm + BOX_H * BOX_W;                           // [TILE_MAXR]
-    float2* cs_s = reinterpret_cast<float2*>(rad_s + TILE_MAXR);  // [N]
-    __shared__ __align__(8) uint64_t bar;
+// The record of one planned sample (same float arithmetic as the planning
+// pass, so the anchor is the one that placed the sample in this tile).
+__global__ void __launch_bounds__(TILE_THREADS) k_tile_records(const __grid_constant__ PlanParams p) {
     const TileItem it = p.items[blockIdx.x];
-    const int bl = blockIdx.y;
-    const uint32_t bar_a = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
-    const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(tile));
+    const int N = p.N;
+    for (int c = threadIdx.x; c < it.cnt; c += TILE_THREADS) {
+        const uint32_t code = p.samples[it.s0 + c];
+        const int ii = (int)(code >> SAMPLE_KBITS);
+        const int j = (int)(code & ((1u << SAMPLE_KBITS) - 1u));
+        float X, Y;
+        sample_xy(p.r * __ldg(&p.rho32[it.i_lo + ii]), __ldg(&p.cs[(it.k_lo + j) & (N - 1)]), p.cx, p.cy, &X, &Y);
+        const float xf = floorf(X), yf = floorf(Y);
+        // the clamp only keeps later shared-memory reads in the box should the
+        // anchor ever differ from the planning pass's
+        const int lx = min(max((int)(xf - (float)it.x_t), 0), TILE_W - 1);
+        const int ly = min(max((int)(yf - (float)it.y_t), 0), TILE_H - 1);
+        p.recs[it.s0 + c] = make_int4(ly * BOX_W + lx, ii * N + ((it.k_lo + j) & (N - 1)), __float_as_int(X - xf),
+                                      __float_as_int(Y - yf));
+    }
+}
+
+// Records [c0, c0 + TILE_G * TILE_THREADS) of the item: this thread's TILE_G
+// of them, all loads issued before any use.
+__device__ __forceinline__ void tile_group(const int4* rec, int cnt, int c0, int4 (&ts)[TILE_G], bool (&on)[TILE_G]) {
+#pragma unroll
+    for (int k = 0; k < TILE_G; ++k) {
+        const int c = c0 + threadIdx.x + k * TILE_THREADS;
+        on[k] = c < cnt;
+        ts[k] = on[k] ? __ldg(&rec[c]) : make_int4(0, 0, 0, 0);
+    }
+}
+
+__device__ __forceinline__ void tile_interp(const float* tile, float* out, const int4 (&ts)[TILE_G],
+                                            const bool (&on)[TILE_G]) {
+    float val[TILE_G];
+#pragma unroll
+    for (int k = 0; k < TILE_G; ++k) {
+        const float* t0p = tile + ts[k].x;
+        const float fx = __int_as_float(ts[k].z), fy = __int_as_float(ts[k].w);
+        const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
+        const float top = fmaf(fx, p01 - p00, p00);
+        const float bot = fmaf(fx, p11 - p10, p10);
+        val[k] = fmaf(fy, bot - top, top);
+    }
+#pragma unroll
+    for (int k = 0; k < TILE_G; ++k)
+        if (on[k]) out[ts[k].y] = val[k];
+}
+
+__device__ __forceinline__ bool tile_try_wait(uint32_t bar) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(ok) : "r"(bar) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a box (phase 0 of its barrier).
+__device__ __forceinline__ bool tile_wait(uint32_t bar) {
+    if (tile_try_wait(bar)) return true;
+    const unsigned long long t0 = tile_ns();
+    while (!tile_try_wait(bar))
+        if (tile_ns() - t0 > TILE_WAIT_NS) return false;
+    return true;
+}
+
+// One CTA per (item, TILE_IPC images): the boxes of its images arrive by TMA
+// while the threads load the records of their first samples, which then serve
+// every image; the rest of a heavy item follows in groups.
+__global__ void __launch_bounds__(TILE_THREADS, TILE_MINB) k_resample_tiles(const __grid_constant__ TileParams p) {
+    extern __shared__ __align__(128) float tile_sm[];          // [TILE_IPC][TILE_BOX_FLOATS]
+    __shared__ __align__(8) uint64_t bar[TILE_IPC];
+    __shared__ int s_ok;
+    const TileItem it = p.items[blockIdx.x];
+    const int b0 = blockIdx.y * TILE_IPC;
+    const int nimg = min(TILE_IPC, p.nb - b0);
+    const uint32_t bar_a = static_cast<uint32_t>(__cvta_generic_to_shared(&bar[0]));
+    const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(tile_sm));
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+        for (int k = 0; k < nimg; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a + 8u * k));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         uint64_t pol;
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
-                     "r"((uint32_t)(BOX_H * BOX_W * 4)) : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-            " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst), "l"(&p.maps[bl]), "r"(it.x_t), "r"(it.y_t), "r"(bar_a),
-            "l"(pol)
-            : "memory");
-    }
-    // while the box is in flight: this item's radii and angle table
-    const int N = p.N;
-    const int nr = it.i_hi - it.i_lo, kn = it.k_n;
-    for (int t = threadIdx.x; t < nr; t += TILE_THREADS) rad_s[t] = p.r * __ldg(&p.rho32[it.i_lo + t]);
-    for (int t = threadIdx.x; t < kn; t += TILE_THREADS) cs_s[t] = __ldg(&p.cs[(it.k_lo + t) & (N - 1)]);
-    // one thread waits for the box (bounded); the others wait at the barrier
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        const unsigned long long t0 = tile_ns();
-        uint32_t ok = 0;
-        while (!ok) {
+        for (int k = 0; k < nimg; ++k) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a + 8u * k),
+                         "r"((uint32_t)(BOX_H * BOX_W * 4)) : "memory");
             asm volatile(
-                "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
-                : "=r"(ok) : "r"(bar_a) : "memory");
-            if (!ok && tile_ns() - t0 > TILE_WAIT_NS) break;
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst + 4u * TILE_BOX_FLOATS * k), "l"(&p.maps[b0 + k]),
+                "r"(it.x_t), "r"(it.y_t), "r"(bar_a + 8u * k), "l"(pol)
+                : "memory");
         }
+    }
+    // while the boxes are in flight: this thread's first samples
+    const int cnt = it.cnt;
+    const int4* rec = p.recs + it.s0;
+    int4 ts[TILE_G];
+    bool on[TILE_G];
+    tile_group(rec, cnt, 0, ts, on);
+    // one thread waits for the boxes (bounded); the others wait at the barrier
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int k = 0; k < nimg && ok; ++k) ok = tile_wait(bar_a + 8u * k);
         if (!ok) {
-            // the copy did not arrive in time: report it and let it drain (bounded)
+            // a copy did not arrive in time: report it and let them drain (bounded)
             atomicExch(p.status, ZM_ETIMEOUT);
-            const unsigned long long t1 = tile_ns();
-            uint32_t late = 0;
-            while (!late && tile_ns() - t1 < TILE_WAIT_NS)
-                asm volatile(
-                    "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n selp.u32 %0, 1, 0, q;\n}\n"
-                    : "=r"(late) : "r"(bar_a) : "memory");
+            for (int k = 0; k < nimg; ++k) tile_wait(bar_a + 8u * k);
         }
         s_ok = ok ? 1 : 0;
     }
     __syncthreads();
     if (!s_ok) return;
 
-    // exactly the samples this tile owns (planned once per geometry)
-    float* out = p.fhat + ((size_t)(p.b_off + bl) * p.n_rho + it.i_lo) * N;
-    const float xt = (float)it.x_t, yt = (float)it.y_t;
-    const int s0 = p.item_off[blockIdx.x];
-    const int cnt = p.item_off[blockIdx.x + 1] - s0;
-    const uint32_t* smp = p.samples + s0;
-    for (int c = threadIdx.x; c < cnt; c += TILE_THREADS) {
-        const uint32_t code = __ldg(&smp[c]);
-        const int ii = (int)(code >> SAMPLE_KBITS);
-        const int j = (int)(code & ((1u << SAMPLE_KBITS) - 1u));
-        float X, Y;
-        sample_xy(rad_s[ii], cs_s[j], p.cx, p.cy, &X, &Y);
-        const float xf = floorf(X), yf = floorf(Y);
-        // the plan put this sample here, so its anchor is inside the tile; the
-        // clamp only keeps shared-memory reads in the box should that ever fail
-        const int lx = min(max((int)(xf - xt), 0), TILE - 1);
-        const int ly = min(max((int)(yf - yt), 0), TILE - 1);
-        const float fx = X - xf, fy = Y - yf;
-        const float* t0p = tile + ly * BOX_W + lx;
-        const float p00 = t0p[0], p01 = t0p[1], p10 = t0p[BOX_W], p11 = t0p[BOX_W + 1];
-        const float top = fmaf(fx, p01 - p00, p00);
-        const float bot = fmaf(fx, p11 - p10, p10);
-        out[(size_t)ii * N + ((it.k_lo + j) & (N - 1))] = fmaf(fy, bot - top, top);
+    const size_t img_stride = (size_t)p.n_rho * p.N;
+    float* out = p.fhat + ((size_t)(p.b_off + b0) * p.n_rho + it.i_lo) * p.N;
+#pragma unroll
+    for (int k = 0; k < TILE_IPC; ++k)
+        if (k < nimg) tile_interp(tile_sm + k * TILE_BOX_FLOATS, out + k * img_stride, ts, on);
+    for (int c0 = TILE_G * TILE_THREADS; c0 < cnt; c0 += TILE_G * TILE_THREADS) {
+        tile_group(rec, cnt, c0, ts, on);
+#pragma unroll
+        for (int k = 0; k < TILE_IPC; ++k)
+            if (k < nimg) tile_interp(tile_sm + k * TILE_BOX_FLOATS, out + k * img_stride, ts, on);
     }
 }
 
@@ -265,15 +341,13 @@ static int encode_map(const zm_image_t& im, CUtensorMap* map) {
 
 struct TileList {
     TileItem* items = nullptr;
-    uint32_t* samples = nullptr;   // packed samples, item after item
-    int* item_off = nullptr;       // [n + 1]
+    int4* recs = nullptr;      // TileRecord of every planned sample, item after item
     int n = 0;
     long long n_samples = 0;
     bool need_zero = false;   // some samples anchor outside every tile (they are 0)
     ~TileList() {
         if (items) cudaFree(items);
-        if (samples) cudaFree(samples);
-        if (item_off) cudaFree(item_off);
+        if (recs) cudaFree(recs);
     }
 };
 
@@ -291,9 +365,10 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
     }
     const double cx = g.cx, cy = g.cy, R = g.r;
     const double rmax = R * rho[n_rho - 1];
-    const int ntx = (g.w + 3 - TILE_X0 + TILE - 1) / TILE;       // covers anchors up to w - 1
-    const int nty = (g.h + 0 - TILE_Y0 + TILE - 1) / TILE;       // covers anchors up to h - 1
-    const double gx0 = TILE_X0, gy0 = TILE_Y0, gx1 = TILE_X0 + (double)ntx * TILE, gy1 = TILE_Y0 + (double)nty * TILE;
+    const int ntx = (g.w + 3 - TILE_X0 + TILE_W - 1) / TILE_W;   // covers anchors up to w - 1
+    const int nty = (g.h + 0 - TILE_Y0 + TILE_H - 1) / TILE_H;   // covers anchors up to h - 1
+    const double gx0 = TILE_X0, gy0 = TILE_Y0, gx1 = TILE_X0 + (double)ntx * TILE_W,
+                 gy1 = TILE_Y0 + (double)nty * TILE_H;
     // samples anchor within +-(rmax + float error) of the centre; those outside
     // the tile grid see only zero pixels and are written by a memset
     const double e = 0.5;
@@ -302,10 +377,10 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
     const double kPi = 3.14159265358979323846, two_pi = 2.0 * kPi;
     for (int ty = 0; ty < nty; ++ty) {
         for (int tx = 0; tx < ntx; ++tx) {
-            const int x_t = TILE_X0 + tx * TILE, y_t = TILE_Y0 + ty * TILE;
+            const int x_t = TILE_X0 + tx * TILE_W, y_t = TILE_Y0 + ty * TILE_H;
             // rectangle in centred coordinates, y up
-            const double u0 = x_t - cx, u1 = x_t + TILE - cx;
-            const double v0 = cy - (y_t + TILE), v1 = cy - y_t;
+            const double u0 = x_t - cx, u1 = x_t + TILE_W - cx;
+            const double v0 = cy - (y_t + TILE_H), v1 = cy - y_t;
             const double du = (u0 > 0) ? u0 : (u1 < 0 ? -u1 : 0.0);
             const double dv = (v0 > 0) ? v0 : (v1 < 0 ? -v1 : 0.0);
             const double dmin = std::sqrt(du * du + dv * dv);
@@ -344,14 +419,19 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
             }
         }
     }
-    std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+#ifndef ZM_TILE_SORT
+#define ZM_TILE_SORT 1
+#endif
+    if (ZM_TILE_SORT)
+        std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
     std::vector<TileItem> h(items.size());
     for (size_t j = 0; j < items.size(); ++j) h[j] = items[j].second;
     tl->n = (int)h.size();
     if (!tl->n) return ZM_OK;
     ZM_CUDA_TRY(cudaMalloc(&tl->items, sizeof(TileItem) * h.size()));
     ZM_CUDA_TRY(cudaMemcpy(tl->items, h.data(), sizeof(TileItem) * h.size(), cudaMemcpyHostToDevice));
-    // plan: count the samples each tile owns, then store them packed
+    // plan: count the samples each tile owns, store them packed, then turn
+    // them into records
     PlanParams pp;
     pp.items = tl->items;
     pp.rho32 = p->rho32;
@@ -360,9 +440,9 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
     pp.cx = g.cx;
     pp.cy = g.cy;
     pp.r = g.r;
-    ZM_CUDA_TRY(cudaMalloc(&pp.counts, sizeof(int) * tl->n));
-    pp.item_off = nullptr;
     pp.samples = nullptr;
+    pp.recs = nullptr;
+    ZM_CUDA_TRY(cudaMalloc(&pp.counts, sizeof(int) * tl->n));
     pp.count_only = 1;
     k_tile_plan<<<tl->n, TILE_THREADS>>>(pp);
     cudaError_t ce = cudaGetLastError();
@@ -371,18 +451,34 @@ static int build_tiles(zm_plan_t p, const GeoImage& g, TileList* tl) {
     cudaFree(pp.counts);
     if (ce != cudaSuccess) return cuda_error(ce, "k_tile_plan (count)");
     count_launch();
-    std::vector<int> off(tl->n + 1, 0);
-    for (int j = 0; j < tl->n; ++j) off[j + 1] = off[j] + cnt[j];
-    tl->n_samples = off[tl->n];
-    ZM_CUDA_TRY(cudaMalloc(&tl->item_off, sizeof(int) * (tl->n + 1)));
-    ZM_CUDA_TRY(cudaMemcpy(tl->item_off, off.data(), sizeof(int) * (tl->n + 1), cudaMemcpyHostToDevice));
-    ZM_CUDA_TRY(cudaMalloc(&tl->samples, sizeof(uint32_t) * std::max<long long>(1, tl->n_samples)));
-    pp.item_off = tl->item_off;
-    pp.samples = tl->samples;
-    pp.count_only = 0;
-    k_tile_plan<<<tl->n, TILE_THREADS>>>(pp);
-    ZM_LAUNCH_CHECK("k_tile_plan");
-    ZM_CUDA_TRY(cudaDeviceSynchronize());
+    long long total = 0;
+    for (int j = 0; j < tl->n; ++j) {
+        h[j].s0 = (int)total;
+        h[j].cnt = cnt[j];
+        total += cnt[j];
+    }
+    if (total >= (1ll << 31)) return set_error(ZM_EINVAL, "too many polar samples for one geometry (%lld)", total);
+    tl->n_samples = total;
+    ZM_CUDA_TRY(cudaMemcpy(tl->items, h.data(), sizeof(TileItem) * h.size(), cudaMemcpyHostToDevice));
+    ZM_CUDA_TRY(cudaMalloc(&pp.samples, sizeof(uint32_t) * std::max<long long>(1, total)));
+    ce = cudaMalloc(&tl->recs, sizeof(int4) * std::max<long long>(1, total));
+    if (ce == cudaSuccess) {
+        pp.recs = tl->recs;
+        pp.count_only = 0;
+        k_tile_plan<<<tl->n, TILE_THREADS>>>(pp);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) {
+            count_launch();
+            k_tile_records<<<tl->n, TILE_THREADS>>>(pp);
+            ce = cudaGetLastError();
+        }
+        if (ce == cudaSuccess) {
+            count_launch();
+            ce = cudaDeviceSynchronize();
+        }
+    }
+    cudaFree(pp.samples);
+    if (ce != cudaSuccess) return cuda_error(ce, "tile plan");
     return ZM_OK;
 }
 
@@ -427,17 +523,11 @@ int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, f
     if (tl->n == 0) return ZM_OK;
     static thread_local TileParams tp;
     tp.items = tl->items;
-    tp.samples = tl->samples;
-    tp.item_off = tl->item_off;
-    tp.rho32 = p->rho32;
-    tp.cs = p->cs;
+    tp.recs = tl->recs;
     tp.fhat = fhat;
     tp.status = p->status;
     tp.n_rho = p->n_rho;
     tp.N = p->n_theta;
-    tp.cx = g.cx;
-    tp.cy = g.cy;
-    tp.r = g.r;
     for (int c0 = 0; c0 < nb; c0 += TILE_MAX_IMG) {
         const int nc = std::min(TILE_MAX_IMG, nb - c0);
         tp.b_off = b0 + c0;
@@ -445,14 +535,18 @@ int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, f
             s = encode_map(imgs[b0 + c0 + j], &tp.maps[j]);
             if (s != ZM_OK) return s;
         }
-        const size_t smem = sizeof(float) * (BOX_H * BOX_W + TILE_MAXR) + sizeof(float2) * (size_t)p->n_theta;
-        int dev = p->device;
-        static size_t configured[64] = {0};
-        if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
-            ZM_CUDA_TRY(cudaFuncSetAttribute(k_resample_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (dev < 64) configured[dev] = smem;
+        tp.nb = nc;
+        const size_t smem = sizeof(float) * TILE_BOX_FLOATS * TILE_IPC;
+        if (smem > 48 * 1024) {
+            static bool configured[64] = {false};
+            const int dev = p->device;
+            if (dev < 0 || dev >= 64 || !configured[dev]) {
+                ZM_CUDA_TRY(
+                    cudaFuncSetAttribute(k_resample_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                if (dev >= 0 && dev < 64) configured[dev] = true;
+            }
         }
-        k_resample_tiles<<<dim3(tl->n, nc), TILE_THREADS, smem, st>>>(tp);
+        k_resample_tiles<<<dim3(tl->n, (nc + TILE_IPC - 1) / TILE_IPC), TILE_THREADS, smem, st>>>(tp);
         ZM_LAUNCH_CHECK("k_resample_tiles");
     }
     return ZM_OK;
