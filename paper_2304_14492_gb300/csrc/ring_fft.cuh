@@ -24,6 +24,43 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// e^{-2 pi i x / 32} for x in [0, 32), from cos(pi k / 16), k = 0..8 and the
+// quadrant symmetries.  Only for x known at compile time (after unrolling),
+// where the table folds into immediates.
+__device__ __forceinline__ float2 w32c(int x) {
+    constexpr float C[9] = {1.0f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f,
+                            0.70710678118654752f, 0.55557023301960218f, 0.38268343236508977f,
+                            0.19509032201612826f, 0.0f};
+    float c, s;
+    if (x <= 8) {
+        c = C[x];
+        s = C[8 - x];
+    } else if (x <= 16) {
+        c = -C[16 - x];
+        s = C[x - 8];
+    } else if (x <= 24) {
+        c = -C[x - 16];
+        s = -C[24 - x];
+    } else {
+        c = C[32 - x];
+        s = -C[x - 24];
+    }
+    return make_float2(c, -s);
+}
+
+// d * W_32^x (d * conj(W_32^x) for INV) with x known at compile time; the
+// quarter turns cost no multiplication.
+template <bool INV>
+__device__ __forceinline__ float2 mul_w32(float2 d, int x) {
+    x &= 31;
+    if (x == 0) return d;
+    if (x == 16) return make_float2(-d.x, -d.y);
+    if (x == 8) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);    // * (+i) : * (-i)
+    if (x == 24) return INV ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);   // * (-i) : * (+i)
+    const float2 w = w32c(x);
+    return cmul(d, INV ? cconj(w) : w);
+}
+
 template <int BITS>
 __host__ __device__ constexpr int brev_c(int x) {
     int r = 0;
@@ -67,9 +104,11 @@ struct RingFFT {
     static constexpr int TBUF = TRANSPOSED ? Q * TSTRIDE : 0;
 
     // In-register Q-point DFT (decimation in frequency): v[r] becomes the
-    // transform at index brev_Q(r); INV uses e^{+2 pi i / Q}.
+    // transform at index brev_Q(r); INV uses e^{+2 pi i / Q}.  The twiddle of
+    // butterfly j at span h is W_Q^{j Q / 2h} = W_32^{16 j / h}, an immediate.
     template <bool INV>
-    __device__ static __forceinline__ void reg_dft(float2 (&v)[Q], const float2* t1) {
+    __device__ static __forceinline__ void reg_dft(float2 (&v)[Q], const float2*) {
+        static_assert(Q <= 32, "in-register DFTs up to 32 points");
 #pragma unroll
         for (int h = Q / 2; h >= 1; h >>= 1) {
 #pragma unroll
@@ -78,13 +117,7 @@ struct RingFFT {
                 for (int j = 0; j < h; ++j) {
                     const float2 x = v[b + j], y = v[b + j + h];
                     v[b + j] = cadd(x, y);
-                    const float2 d = csub(x, y);
-                    if (j == 0) {
-                        v[b + j + h] = d;
-                    } else {
-                        const float2 w = t1[j * (Q / (2 * h))];
-                        v[b + j + h] = cmul(d, INV ? cconj(w) : w);
-                    }
+                    v[b + j + h] = mul_w32<INV>(csub(x, y), 16 * j / h);
                 }
             }
         }
@@ -116,22 +149,9 @@ struct RingFFT {
     // Forward DFT X_k = sum_j z_j e^{-2 pi i j k / M}; `tab` from
     // load_twiddles().  All 32 lanes must call; lanes >= L carry dummy data.
     __device__ static __forceinline__ void forward(float2 (&v)[Q], int t, const float2* tab) {
-        const float2* t1 = tab;
         const float2* t2 = tab + TW_T1;
         const float2* t3 = t2 + Q * L;
-#pragma unroll
-        for (int h = Q / 2; h >= 1; h >>= 1) {
-#pragma unroll
-            for (int b = 0; b < Q; b += 2 * h) {
-#pragma unroll
-                for (int j = 0; j < h; ++j) {
-                    const float2 x = v[b + j], y = v[b + j + h];
-                    v[b + j] = cadd(x, y);
-                    const float2 d = csub(x, y);
-                    v[b + j + h] = (j == 0) ? d : cmul(d, t1[j * (Q / (2 * h))]);
-                }
-            }
-        }
+        reg_dft<false>(v, tab);
         const int tl = t & (L - 1);
 #pragma unroll
         for (int r = 1; r < Q; ++r) v[r] = cmul(v[r], t2[brev_c<LOGQ>(r) * L + tl]);
@@ -139,13 +159,14 @@ struct RingFFT {
         for (int lg = LOGL - 1; lg >= 0; --lg) {
             const int h = 1 << lg;
             const bool upper = (t & h) != 0;
-            const float2 w = t3[lg * L + tl];
+            const float2 w = t3[lg * L + tl];      // W_2h^{t mod h}; 1 at h = 1
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 float2 p;
                 p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
                 p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
-                v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
+                if (h == 1) v[r] = upper ? csub(p, v[r]) : cadd(v[r], p);
+                else v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
             }
         }
     }
@@ -158,7 +179,6 @@ struct RingFFT {
     // i.e. an L-point DFT across lanes (decimation in time, bit-reversed input),
     // a twiddle, and a Q-point DFT in registers (decimation in frequency).
     __device__ static __forceinline__ void inverse_natural(float2 (&v)[Q], int t, const float2* tab) {
-        const float2* t1 = tab;
         const float2* t2 = tab + TW_T1;
         const float2* t3 = t2 + Q * L;
         const int tl = t & (L - 1);
@@ -166,30 +186,19 @@ struct RingFFT {
         for (int lg = 0; lg < LOGL; ++lg) {
             const int h = 1 << lg;
             const bool upper = (t & h) != 0;
-            const float2 w = cconj(t3[lg * L + tl]);
+            const float2 w = cconj(t3[lg * L + tl]);     // 1 at h = 1
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 float2 p;
                 p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
                 p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
-                v[r] = upper ? csub(p, cmul(w, v[r])) : cadd(v[r], cmul(w, p));
+                if (h == 1) v[r] = upper ? csub(p, v[r]) : cadd(v[r], p);
+                else v[r] = upper ? csub(p, cmul(w, v[r])) : cadd(v[r], cmul(w, p));
             }
         }
 #pragma unroll
         for (int a = 1; a < Q; ++a) v[a] = cmul(v[a], cconj(t2[a * L + tl]));
-#pragma unroll
-        for (int h = Q / 2; h >= 1; h >>= 1) {
-#pragma unroll
-            for (int b = 0; b < Q; b += 2 * h) {
-#pragma unroll
-                for (int j = 0; j < h; ++j) {
-                    const float2 x = v[b + j], y = v[b + j + h];
-                    v[b + j] = cadd(x, y);
-                    const float2 d = csub(x, y);
-                    v[b + j + h] = (j == 0) ? d : cmul(d, cconj(t1[j * (Q / (2 * h))]));
-                }
-            }
-        }
+        reg_dft<true>(v, tab);
     }
 
     __device__ static __forceinline__ int brev_g(int g) {
@@ -217,18 +226,28 @@ struct RingFFT {
         for (int u = 0; u < Q; ++u) v[u] = buf[k1 * TSTRIDE + g + G * u];
         __syncwarp();
         reg_dft<false>(v, t1);
+        if constexpr (G == 2) {
+            // W_32^{g brev(r)}, g in {0, 1}: an immediate or 1
 #pragma unroll
-        for (int r = 1; r < Q; ++r) v[r] = cmul(v[r], t32[g * brev_c<LOGQ>(r)]);
+            for (int r = 1; r < Q; ++r) {
+                const float2 m = mul_w32<false>(v[r], brev_c<LOGQ>(r));
+                v[r] = g ? m : v[r];
+            }
+        } else if constexpr (G > 2) {
+#pragma unroll
+            for (int r = 1; r < Q; ++r) v[r] = cmul(v[r], t32[g * brev_c<LOGQ>(r)]);
+        }
 #pragma unroll
         for (int h = G / 2; h >= 1; h >>= 1) {
             const bool upper = (g & h) != 0;
-            const float2 w = t32[(g & (h - 1)) * (16 / h)];
+            const float2 w = t32[(g & (h - 1)) * (16 / h)];     // 1 at h = 1
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 float2 p;
                 p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
                 p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
-                v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
+                if (h == 1) v[r] = upper ? csub(p, v[r]) : cadd(v[r], p);
+                else v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
             }
         }
     }
@@ -245,17 +264,26 @@ struct RingFFT {
         for (int lg = 0; lg < LOGG; ++lg) {
             const int h = 1 << lg;
             const bool upper = (g & h) != 0;
-            const float2 w = cconj(t32[(g & (h - 1)) * (16 / h)]);
+            const float2 w = cconj(t32[(g & (h - 1)) * (16 / h)]);     // 1 at h = 1
 #pragma unroll
             for (int r = 0; r < Q; ++r) {
                 float2 p;
                 p.x = __shfl_xor_sync(0xffffffffu, v[r].x, h);
                 p.y = __shfl_xor_sync(0xffffffffu, v[r].y, h);
-                v[r] = upper ? csub(p, cmul(w, v[r])) : cadd(v[r], cmul(w, p));
+                if (h == 1) v[r] = upper ? csub(p, v[r]) : cadd(v[r], p);
+                else v[r] = upper ? csub(p, cmul(w, v[r])) : cadd(v[r], cmul(w, p));
             }
         }
+        if constexpr (G == 2) {
 #pragma unroll
-        for (int a = 1; a < Q; ++a) v[a] = cmul(v[a], cconj(t32[g * a]));
+            for (int a = 1; a < Q; ++a) {
+                const float2 m = mul_w32<true>(v[a], a);
+                v[a] = g ? m : v[a];
+            }
+        } else if constexpr (G > 2) {
+#pragma unroll
+            for (int a = 1; a < Q; ++a) v[a] = cmul(v[a], cconj(t32[g * a]));
+        }
         reg_dft<true>(v, t1);
         __syncwarp();
 #pragma unroll
