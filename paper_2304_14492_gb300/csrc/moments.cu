@@ -2,6 +2,8 @@
 // every ring (the e^{-j m theta} factor), then the radial projection with the
 // (n+1)/pi weight, and the Neumann factor of Eq. 14-15.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "ring_fft.cuh"
 #include "zm_internal.cuh"
@@ -24,6 +26,7 @@ constexpr int KB_MAX_IMG = 128;
 
 struct KbParams {
     int n_rho, n_max, batch_total, b_off;
+    int nb;                // images in this launch
     const float* rho32;    // [n_rho]
     const float2* cs;      // [N] (cos theta_k, sin theta_k)
     const float2* tw;      // [N] e^{-2 pi i j / N}
@@ -55,10 +58,13 @@ __device__ __forceinline__ float bilinear(const GeoImage& im, float X, float Y) 
     return fmaf(fy, bot - top, top);
 }
 
-// One CTA = R consecutive rings of one image, one warp per ring (R = blockDim/32).
-// Phase 1: the R x N samples into shared memory (bilinear gather, or a copy of
-// given polar samples).  Phase 2: per warp, the N-point real FFT of its ring
-// as an N/2-point complex FFT plus the split
+// One CTA = R consecutive rings of one image at a time, one warp per ring
+// (R = blockDim/32); the grid is persistent and each CTA walks ring blocks
+// (image, block) after loading the FFT twiddles once.
+// Phase 1: the R x N samples into shared memory (bilinear gather; polar input
+// goes straight from global memory into the FFT registers).  Phase 2: per
+// warp, the N-point real FFT of its ring as an N/2-point complex FFT plus the
+// split
 //   F_m = (Z_m + conj Z_{M-m})/2 + e^{-2 pi i m/N} (Z_m - conj Z_{M-m})/(2i),
 // for m = 0..n_max.  Phase 3: F[m][b][re/im][i0..i0+R) written as segments.
 template <int LOGN, int MODE>
@@ -69,93 +75,97 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
     extern __shared__ __align__(16) float smem[];
     const int R = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bl = blockIdx.y;
-    const int b = p.b_off + bl;
-    const int i0 = blockIdx.x * R;
     const int n_rho = p.n_rho;
-    float* rings = smem;
-
-    if (MODE == KB_POLAR) {
-        // samples go straight from global memory into the FFT registers below
-    } else {
-        const GeoImage im = p.img[bl];
-#pragma unroll 4
-        for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-            const int r = idx >> LOGN, k = idx & (N - 1);
-            const int i = i0 + r;
-            float v = 0.f;
-            if (i < n_rho) {
-                const float rad = im.r * __ldg(&p.rho32[i]);
-                const float2 c = __ldg(&p.cs[k]);
-                v = bilinear(im, fmaf(rad, c.x, im.cx), fmaf(-rad, c.y, im.cy));
-                if (p.fhat_out) p.fhat_out[((size_t)b * n_rho + i) * N + k] = v;
-            }
-            rings[r * ROW + k] = v;
-        }
-    }
-    if (MODE == KB_RESAMPLE) return;
     const int n_max = p.n_max;
+    float* rings = smem;
     float* Fs = smem + R * ROW;                  // [2][n_max+1][R]
     float2* twt = reinterpret_cast<float2*>(smem + ((R * ROW + 2 * (n_max + 1) * R + 1) & ~1));
     float2* twm = twt + FFT::TW_FLOAT2;            // e^{-2 pi i m / N}, m <= n_max
-    FFT::load_twiddles(twt, p.tw);
-    for (int m = threadIdx.x; m <= n_max; m += blockDim.x) twm[m] = __ldg(&p.tw[m]);
-    __syncthreads();
-
-    {
-        float* row = rings + warp * ROW;
-        float2 v[FFT::Q];
-        if (MODE == KB_POLAR) {
-            const int i = i0 + warp;
-            const bool live = lane < FFT::L && i < n_rho;
-            const float* src = p.fhat_in + ((size_t)b * n_rho + (live ? i : 0)) * N;
-            if ((reinterpret_cast<uintptr_t>(p.fhat_in) & 7) == 0) {
-                const float2* z = reinterpret_cast<const float2*>(src);
-#pragma unroll
-                for (int s = 0; s < FFT::Q; ++s) v[s] = live ? __ldg(&z[lane + FFT::L * s]) : make_float2(0.f, 0.f);
-            } else {
-#pragma unroll
-                for (int s = 0; s < FFT::Q; ++s) {
-                    const int j = lane + FFT::L * s;
-                    v[s] = live ? make_float2(__ldg(src + 2 * j), __ldg(src + 2 * j + 1)) : make_float2(0.f, 0.f);
-                }
-            }
-        } else {
-            const float2* z = reinterpret_cast<const float2*>(row);
-#pragma unroll
-            for (int s = 0; s < FFT::Q; ++s)
-                v[s] = (lane < FFT::L) ? z[lane + FFT::L * s] : make_float2(0.f, 0.f);
-            __syncwarp();
-        }
-        float2* X = reinterpret_cast<float2*>(row);
-        FFT::fwd(v, lane, twt, X);                 // the row doubles as the transpose buffer
-        if (lane < FFT::L) {
-#pragma unroll
-            for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::fwd_index(r, lane))] = v[r];
-        }
-        __syncwarp();
-        for (int m = lane; m <= n_max; m += 32) {
-            const float2 A = X[FFT::pad(m)];
-            const float2 B = cconj(X[FFT::pad((FFT::M - m) & (FFT::M - 1))]);
-            const float2 E = cscale(cadd(A, B), 0.5f);
-            const float2 D = csub(A, B);
-            const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-            const float2 Fm = cadd(E, cmul(twm[m], O));
-            Fs[m * R + warp] = Fm.x;
-            Fs[((n_max + 1) + m) * R + warp] = Fm.y;
-        }
+    if (MODE != KB_RESAMPLE) {
+        FFT::load_twiddles(twt, p.tw);
+        for (int m = threadIdx.x; m <= n_max; m += blockDim.x) twm[m] = __ldg(&p.tw[m]);
     }
-    __syncthreads();
-    const int lgR = __ffs(R) - 1;                 // R is a power of two
-    const int nm1 = n_max + 1;
-    const int tot = 2 * nm1 * R;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int r = e & (R - 1);
-        const int cm = e >> lgR;
-        const int c = cm >= nm1 ? 1 : 0;
-        const int m = cm - c * nm1;
-        const int i = i0 + r;
-        if (i < n_rho) p.F[(((size_t)m * p.batch_total + b) * 2 + c) * n_rho + i] = Fs[e];
+    const int n_rb = (n_rho + R - 1) / R;
+    for (int item = blockIdx.x; item < n_rb * p.nb; item += gridDim.x) {
+        const int bl = item / n_rb;
+        const int i0 = (item - bl * n_rb) * R;
+        const int b = p.b_off + bl;
+        if (MODE != KB_POLAR) {
+            const GeoImage im = p.img[bl];
+#pragma unroll 4
+            for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+                const int r = idx >> LOGN, k = idx & (N - 1);
+                const int i = i0 + r;
+                float v = 0.f;
+                if (i < n_rho) {
+                    const float rad = im.r * __ldg(&p.rho32[i]);
+                    const float2 c = __ldg(&p.cs[k]);
+                    v = bilinear(im, fmaf(rad, c.x, im.cx), fmaf(-rad, c.y, im.cy));
+                    if (p.fhat_out) p.fhat_out[((size_t)b * n_rho + i) * N + k] = v;
+                }
+                if (MODE != KB_RESAMPLE) rings[r * ROW + k] = v;
+            }
+        }
+        if (MODE == KB_RESAMPLE) continue;
+        __syncthreads();   // the twiddles (first block) and the gathered rings
+
+        {
+            float* row = rings + warp * ROW;
+            float2 v[FFT::Q];
+            if (MODE == KB_POLAR) {
+                const int i = i0 + warp;
+                const bool live = lane < FFT::L && i < n_rho;
+                const float* src = p.fhat_in + ((size_t)b * n_rho + (live ? i : 0)) * N;
+                if ((reinterpret_cast<uintptr_t>(p.fhat_in) & 7) == 0) {
+                    const float2* z = reinterpret_cast<const float2*>(src);
+#pragma unroll
+                    for (int s = 0; s < FFT::Q; ++s)
+                        v[s] = live ? __ldg(&z[lane + FFT::L * s]) : make_float2(0.f, 0.f);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < FFT::Q; ++s) {
+                        const int j = lane + FFT::L * s;
+                        v[s] = live ? make_float2(__ldg(src + 2 * j), __ldg(src + 2 * j + 1)) : make_float2(0.f, 0.f);
+                    }
+                }
+            } else {
+                const float2* z = reinterpret_cast<const float2*>(row);
+#pragma unroll
+                for (int s = 0; s < FFT::Q; ++s)
+                    v[s] = (lane < FFT::L) ? z[lane + FFT::L * s] : make_float2(0.f, 0.f);
+                __syncwarp();
+            }
+            float2* X = reinterpret_cast<float2*>(row);
+            FFT::fwd(v, lane, twt, X);                 // the row doubles as the transpose buffer
+            if (lane < FFT::L) {
+#pragma unroll
+                for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::fwd_index(r, lane))] = v[r];
+            }
+            __syncwarp();
+            for (int m = lane; m <= n_max; m += 32) {
+                const float2 A = X[FFT::pad(m)];
+                const float2 B = cconj(X[FFT::pad((FFT::M - m) & (FFT::M - 1))]);
+                const float2 E = cscale(cadd(A, B), 0.5f);
+                const float2 D = csub(A, B);
+                const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+                const float2 Fm = cadd(E, cmul(twm[m], O));
+                Fs[m * R + warp] = Fm.x;
+                Fs[((n_max + 1) + m) * R + warp] = Fm.y;
+            }
+        }
+        __syncthreads();
+        const int lgR = __ffs(R) - 1;                 // R is a power of two
+        const int nm1 = n_max + 1;
+        const int tot = 2 * nm1 * R;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int r = e & (R - 1);
+            const int cm = e >> lgR;
+            const int c = cm >= nm1 ? 1 : 0;
+            const int m = cm - c * nm1;
+            const int i = i0 + r;
+            if (i < n_rho) p.F[(((size_t)m * p.batch_total + b) * 2 + c) * n_rho + i] = Fs[e];
+        }
+        __syncthreads();   // rings and Fs are refilled for the next block
     }
 }
 
@@ -173,7 +183,26 @@ static int launch_kb_t(const KbParams& kp, int R, int nb, cudaStream_t st) {
                                          (int)smem));
         if (dev < 64) configured[dev] = smem;
     }
-    dim3 grid((kp.n_rho + R - 1) / R, nb);
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, int> resident;   // (R, smem) -> CTAs per SM
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = resident.find({R, smem});
+        if (it != resident.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ring_spectra<LOGN, MODE>, R * 32, smem) !=
+                    cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            resident[{R, smem}] = per_sm;
+        }
+    }
+    KbParams& k = const_cast<KbParams&>(kp);
+    k.nb = nb;
+    const long long items = (long long)((kp.n_rho + R - 1) / R) * nb;
+    const int grid = (int)std::min<long long>(items, (long long)per_sm * num_sms(dev));
     k_ring_spectra<LOGN, MODE><<<grid, R * 32, smem, st>>>(kp);
     ZM_LAUNCH_CHECK("k_ring_spectra");
     return ZM_OK;

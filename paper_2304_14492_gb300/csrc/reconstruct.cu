@@ -3,6 +3,8 @@
 // ring, and optional interpolation onto pixels; the reconstruction errors of
 // Eq. 10 and Eq. 13 and the min-max normalisation of Sec. 3 / Table I.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "ring_fft.cuh"
 #include "zm_internal.cuh"
@@ -83,16 +85,17 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // is the M-point inverse DFT of
 //   C_m = (S_m + conj S_{M-m}) + i e^{2 pi i m/N} (S_m - conj S_{M-m}).
 // One warp per ring: C is formed straight from G in shared memory in the
-// order inverse_natural() wants, and its output is already in natural order
+// order the inverse FFT wants, and its output is already in natural order
 // across lanes, so f~ is written (and the reference read) with coalesced
-// accesses from registers.
+// accesses from registers.  The grid is persistent: each CTA loads the
+// twiddles once and walks blocks of R rings (b, rb).
 // With ERR, the CTA also accumulates, against the reference polar samples
-// `ref`, sum (ref - f~)^2, sum ref^2, max ref and the node count over its rings
-// into one record part[b][blockIdx.x] (Eq. 10 / Eq. 13 on the polar nodes); `out`
-// may then be NULL.
+// `ref`, sum (ref - f~)^2, sum ref^2, max ref and the node count over the rings
+// of a block into one record part[b][rb] (Eq. 10 / Eq. 13 on the polar nodes);
+// `out` may then be NULL.
 template <int LOGN, bool ERR>
 __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4))
-k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho,
+k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho, int batch,
              float* __restrict__ out, const float* __restrict__ ref, double* __restrict__ part) {
     using FFT = RingFFT<LOGN>;
     constexpr int N = FFT::N;
@@ -103,106 +106,126 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     __shared__ float red[8][4];
     const int R = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.y;
-    const int i0 = blockIdx.x * R;
     const int nm1 = n_max + 1;
     float2* twt = Gs + R * nm1;                                   // warp-FFT twiddles
     float2* twm = twt + FFT::TW_FLOAT2;                           // e^{-2 pi i m / N}, m < M
     float2* tbuf = twm + M + warp * FFT::TBUF;                    // per-warp transpose buffer
     FFT::load_twiddles(twt, tw);
     for (int m = threadIdx.x; m < M; m += blockDim.x) twm[m] = __ldg(&tw[m]);
-    for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
-        const int r = e % R, m = e / R;
-        const int i = i0 + r;
-        float2 g = make_float2(0.f, 0.f);
-        if (i < n_rho) {
-            const float* gp = G + (((size_t)b * nm1 + m) * 2) * n_rho + i;
-            g = make_float2(__ldg(gp), __ldg(gp + n_rho));
-        }
-        Gs[r * nm1 + m] = g;
-    }
-    __syncthreads();
-    const float2* Gr = Gs + warp * nm1;
-    float2 v[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        const int m = FFT::inv_index(a, lane);
-        float2 Sm = make_float2(0.f, 0.f), T = make_float2(0.f, 0.f);
-        if (m <= n_max) Sm = (m == 0) ? make_float2(2.f * Gr[0].x, 0.f) : Gr[m];
-        const int q = M - m;
-        if (q >= 1 && q <= n_max) T = cconj(Gr[q]);
-        const float2 w = twm[m];                         // e^{-2 pi i m/N}
-        const float2 ie = make_float2(w.y, w.x);         // i e^{+2 pi i m/N} = i conj(w)
-        const float2 C = cadd(cadd(Sm, T), cmul(ie, csub(Sm, T)));
-        v[a] = (lane < L) ? C : make_float2(0.f, 0.f);
-    }
-    FFT::inv(v, lane, twt, tbuf);
-    const int i = i0 + warp;
-    float sd = 0.f, sf = 0.f, mx = -INFINITY, cnt = 0.f;
-    if (i < n_rho && lane < L) {
-        const size_t row = ((size_t)b * n_rho + i) * N;
-        float2* o = out ? reinterpret_cast<float2*>(out + row) : nullptr;
-        if (ERR) {
-            const float2* rf = reinterpret_cast<const float2*>(ref + row);
-            // groups of four loads in flight, consumed as they arrive (few live registers)
-#pragma unroll
-            for (int r0 = 0; r0 < Q; r0 += 4) {
-                float2 f[4];
-#pragma unroll
-                for (int u = 0; u < 4 && r0 + u < Q; ++u) f[u] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r0 + u)]);
-#pragma unroll
-                for (int u = 0; u < 4 && r0 + u < Q; ++u) {
-                    const int r = r0 + u;
-                    const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
-                    if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
-                    const float d0 = f[u].x - x.x, d1 = f[u].y - x.y;
-                    sd = fmaf(d0, d0, fmaf(d1, d1, sd));
-                    sf = fmaf(f[u].x, f[u].x, fmaf(f[u].y, f[u].y, sf));
-                    mx = fmaxf(mx, fmaxf(f[u].x, f[u].y));
-                    cnt += 2.f;
-                }
+    // persistent: the CTA takes ring blocks (b, rb) = item / n_rb, item mod n_rb
+    const int n_rb = (n_rho + R - 1) / R;
+    for (int item = blockIdx.x; item < n_rb * batch; item += gridDim.x) {
+        const int b = item / n_rb, rb = item - b * n_rb;
+        const int i0 = rb * R;
+        for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
+            const int r = e % R, m = e / R;
+            const int i = i0 + r;
+            float2 g = make_float2(0.f, 0.f);
+            if (i < n_rho) {
+                const float* gp = G + (((size_t)b * nm1 + m) * 2) * n_rho + i;
+                g = make_float2(__ldg(gp), __ldg(gp + n_rho));
             }
-        } else {
-#pragma unroll
-            for (int r = 0; r < Q; ++r)
-                o[lane + L * brev_c<FFT::LOGQ>(r)] = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
-        }
-    }
-    if (ERR) {
-        for (int o2 = 16; o2; o2 >>= 1) {
-            sd += __shfl_xor_sync(0xffffffffu, sd, o2);
-            sf += __shfl_xor_sync(0xffffffffu, sf, o2);
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
-        }
-        if (lane == 0) {
-            red[warp][0] = sd;
-            red[warp][1] = sf;
-            red[warp][2] = mx;
-            red[warp][3] = cnt;
+            Gs[r * nm1 + m] = g;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0, c = 0, n = 0;
-            float m = -INFINITY;
-            for (int w = 0; w < R; ++w) {
-                a += red[w][0];
-                c += red[w][1];
-                m = fmaxf(m, red[w][2]);
-                n += red[w][3];
-            }
-            double* o = part + ((size_t)b * gridDim.x + blockIdx.x) * 4;
-            o[0] = a;
-            o[1] = c;
-            o[2] = (double)m;
-            o[3] = n;
+        const float2* Gr = Gs + warp * nm1;
+        float2 v[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int m = FFT::inv_index(a, lane);
+            float2 Sm = make_float2(0.f, 0.f), T = make_float2(0.f, 0.f);
+            if (m <= n_max) Sm = (m == 0) ? make_float2(2.f * Gr[0].x, 0.f) : Gr[m];
+            const int q = M - m;
+            if (q >= 1 && q <= n_max) T = cconj(Gr[q]);
+            const float2 w = twm[m];                         // e^{-2 pi i m/N}
+            const float2 ie = make_float2(w.y, w.x);         // i e^{+2 pi i m/N} = i conj(w)
+            const float2 C = cadd(cadd(Sm, T), cmul(ie, csub(Sm, T)));
+            v[a] = (lane < L) ? C : make_float2(0.f, 0.f);
         }
+        FFT::inv(v, lane, twt, tbuf);
+        const int i = i0 + warp;
+        float sd = 0.f, sf = 0.f, mx = -INFINITY, cnt = 0.f;
+        if (i < n_rho && lane < L) {
+            const size_t row = ((size_t)b * n_rho + i) * N;
+            float2* o = out ? reinterpret_cast<float2*>(out + row) : nullptr;
+            if (ERR) {
+                const float2* rf = reinterpret_cast<const float2*>(ref + row);
+                // groups of four loads in flight, consumed as they arrive (few live registers)
+#pragma unroll
+                for (int r0 = 0; r0 < Q; r0 += 4) {
+                    float2 f[4];
+#pragma unroll
+                    for (int u = 0; u < 4 && r0 + u < Q; ++u) f[u] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r0 + u)]);
+#pragma unroll
+                    for (int u = 0; u < 4 && r0 + u < Q; ++u) {
+                        const int r = r0 + u;
+                        const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
+                        if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
+                        const float d0 = f[u].x - x.x, d1 = f[u].y - x.y;
+                        sd = fmaf(d0, d0, fmaf(d1, d1, sd));
+                        sf = fmaf(f[u].x, f[u].x, fmaf(f[u].y, f[u].y, sf));
+                        mx = fmaxf(mx, fmaxf(f[u].x, f[u].y));
+                        cnt += 2.f;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < Q; ++r)
+                    o[lane + L * brev_c<FFT::LOGQ>(r)] = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
+            }
+        }
+        if (ERR) {
+            for (int o2 = 16; o2; o2 >>= 1) {
+                sd += __shfl_xor_sync(0xffffffffu, sd, o2);
+                sf += __shfl_xor_sync(0xffffffffu, sf, o2);
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
+            }
+            if (lane == 0) {
+                red[warp][0] = sd;
+                red[warp][1] = sf;
+                red[warp][2] = mx;
+                red[warp][3] = cnt;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double a = 0, c = 0, n = 0;
+                float m = -INFINITY;
+                for (int w = 0; w < R; ++w) {
+                    a += red[w][0];
+                    c += red[w][1];
+                    m = fmaxf(m, red[w][2]);
+                    n += red[w][3];
+                }
+                double* o = part + ((size_t)b * n_rb + rb) * 4;
+                o[0] = a;
+                o[1] = c;
+                o[2] = (double)m;
+                o[3] = n;
+            }
+        }
+        __syncthreads();   // Gs and red are refilled for the next ring block
     }
+}
+
+// Resident CTAs per SM of a kernel at a dynamic shared-memory size (cached).
+template <typename K>
+static int resident_blocks(K kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(reinterpret_cast<const void*>(kernel), smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    cache[key] = n;
+    return n;
 }
 
 template <int LOGN, bool ERR>
 static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho, int batch, float* out,
-                         const float* ref, double* part, cudaStream_t st) {
+                         const float* ref, double* part, int sms, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const int R = 8;
     const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2 + FFT::M + (size_t)R * FFT::TBUF);
@@ -214,8 +237,10 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
                                          (int)smem));
         if (dev < 64) configured[dev] = smem;
     }
-    dim3 grid((n_rho + R - 1) / R, batch);
-    k_recon_ifft<LOGN, ERR><<<grid, R * 32, smem, st>>>(G, tw, n_max, n_rho, out, ref, part);
+    const long long items = (long long)((n_rho + R - 1) / R) * batch;
+    const int slots = sms * resident_blocks(k_recon_ifft<LOGN, ERR>, R * 32, smem);
+    const int grid = (int)std::min<long long>(items, slots);
+    k_recon_ifft<LOGN, ERR><<<grid, R * 32, smem, st>>>(G, tw, n_max, n_rho, batch, out, ref, part);
     ZM_LAUNCH_CHECK("k_recon_ifft");
     return ZM_OK;
 }
@@ -223,16 +248,23 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
 template <bool ERR>
 static int launch_ifft(zm_plan_t p, const float* G, int batch, float* out, const float* ref, double* part,
                        cudaStream_t st) {
+    static int sms_cache[64] = {0};
+    const int dev = p->device;
+    int sms = (dev >= 0 && dev < 64) ? sms_cache[dev] : 0;
+    if (!sms) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        if (dev >= 0 && dev < 64) sms_cache[dev] = sms;
+    }
     switch (p->log_theta) {
-        case 3: return launch_ifft_t<3, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 4: return launch_ifft_t<4, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 5: return launch_ifft_t<5, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 6: return launch_ifft_t<6, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 7: return launch_ifft_t<7, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 8: return launch_ifft_t<8, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 9: return launch_ifft_t<9, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 10: return launch_ifft_t<10, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
-        case 11: return launch_ifft_t<11, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, st);
+        case 3: return launch_ifft_t<3, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 4: return launch_ifft_t<4, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 5: return launch_ifft_t<5, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 6: return launch_ifft_t<6, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 7: return launch_ifft_t<7, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 8: return launch_ifft_t<8, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 9: return launch_ifft_t<9, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 10: return launch_ifft_t<10, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 11: return launch_ifft_t<11, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
         default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", p->log_theta);
     }
 }
