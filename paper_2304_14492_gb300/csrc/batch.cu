@@ -109,9 +109,7 @@ static int enqueue_batch(zm_batch_t b, const zm_request_t* reqs, unsigned flags,
         imgs.clear();
         for (int r : g.members) imgs.push_back(reqs[r].image);
         const int gb = (int)g.members.size();
-        float* F = (float*)g.plan->ws_F.ptr;
-        int s = launch_spectra(g.plan, imgs.data(), nullptr, gb, F, nullptr, false, st);
-        if (s == ZM_OK) s = launch_projection(g.plan, F, gb, g.out_buf, flags, st);
+        const int s = launch_moments(g.plan, imgs.data(), nullptr, gb, g.out_buf, nullptr, flags, st);
         if (s != ZM_OK) return s;
     }
     k_batch_copy<<<(unsigned)b->reqs.size(), 256, 0, st>>>(b->d_copy);
@@ -197,15 +195,13 @@ static int time_group(zm_batch_t b, BatchGroup& g, const zm_request_t* reqs, dou
     std::vector<zm_image_t> imgs;
     for (int r : g.members) imgs.push_back(reqs[r].image);
     const int gb = (int)g.members.size();
-    float* F = (float*)g.plan->ws_F.ptr;
     cudaEvent_t e0, e1;
     ZM_CUDA_TRY(cudaEventCreate(&e0));
     ZM_CUDA_TRY(cudaEventCreate(&e1));
     int s = ZM_OK;
     for (int it = 0; it < 4 && s == ZM_OK; ++it) {
         if (it == 1) cudaEventRecord(e0, b->cap);
-        s = launch_spectra(g.plan, imgs.data(), nullptr, gb, F, nullptr, false, b->cap);
-        if (s == ZM_OK) s = launch_projection(g.plan, F, gb, g.out_buf, 0, b->cap);
+        s = launch_moments(g.plan, imgs.data(), nullptr, gb, g.out_buf, nullptr, 0, b->cap);
     }
     cudaEventRecord(e1, b->cap);
     cudaError_t e = cudaEventSynchronize(e1);

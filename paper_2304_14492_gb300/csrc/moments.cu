@@ -1,6 +1,8 @@
 // Moments (Eq. 1): bilinear polar resampling (Sec. 2.5) fused with a real FFT of
 // every ring (the e^{-j m theta} factor), then the radial projection with the
 // (n+1)/pi weight, and the Neumann factor of Eq. 14-15.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -27,6 +29,9 @@ constexpr int KB_MAX_IMG = 128;
 struct KbParams {
     int n_rho, n_max, batch_total, b_off;
     int nb;                // images in this launch
+    uint8_t* Fblk;         // bf16 hi / lo operand blocks of F (R = 8), or NULL
+    size_t fblk_half;      // bytes of one half
+    int n_chunks;          // 64-node chunks of the radial index
     const float* rho32;    // [n_rho]
     const float2* cs;      // [N] (cos theta_k, sin theta_k)
     const float2* tw;      // [N] e^{-2 pi i j / N}
@@ -85,7 +90,9 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
         FFT::load_twiddles(twt, p.tw);
         for (int m = threadIdx.x; m <= n_max; m += blockDim.x) twm[m] = __ldg(&p.tw[m]);
     }
-    const int n_rb = (n_rho + R - 1) / R;
+    // with operand blocks, ring blocks run up to the last 64-node chunk (rings
+    // past n_rho are zero), so that every block of the chunk is written
+    const int n_rb = p.Fblk ? p.n_chunks * (64 / R) : (n_rho + R - 1) / R;
     for (int item = blockIdx.x; item < n_rb * p.nb; item += gridDim.x) {
         const int bl = item / n_rb;
         const int i0 = (item - bl * n_rb) * R;
@@ -154,16 +161,38 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
             }
         }
         __syncthreads();
-        const int lgR = __ffs(R) - 1;                 // R is a power of two
         const int nm1 = n_max + 1;
-        const int tot = 2 * nm1 * R;
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            const int r = e & (R - 1);
-            const int cm = e >> lgR;
-            const int c = cm >= nm1 ? 1 : 0;
-            const int m = cm - c * nm1;
-            const int i = i0 + r;
-            if (i < n_rho) p.F[(((size_t)m * p.batch_total + b) * 2 + c) * n_rho + i] = Fs[e];
+        if (p.Fblk) {
+            // R = 8 rings = one 16-byte row per (m, re/im): bf16 hi and lo halves
+            const int ncol = 2 * p.batch_total;
+            for (int e = threadIdx.x; e < 2 * nm1; e += blockDim.x) {
+                const int c = e >= nm1 ? 1 : 0;
+                const int m = e - c * nm1;
+                const float* src = Fs + (size_t)e * 8;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(src[2 * q]), h1 = __float2bfloat16_rn(src[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(src[2 * q] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(src[2 * q + 1] - __bfloat162float(h1));
+                    h[q] = __bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    l[q] = __bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                const size_t o = fblk_row(m, i0, 2 * b + c, p.n_chunks, ncol);
+                *reinterpret_cast<uint4*>(p.Fblk + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(p.Fblk + p.fblk_half + o) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        } else {
+            const int lgR = __ffs(R) - 1;                 // R is a power of two
+            const int tot = 2 * nm1 * R;
+            for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+                const int r = e & (R - 1);
+                const int cm = e >> lgR;
+                const int c = cm >= nm1 ? 1 : 0;
+                const int m = cm - c * nm1;
+                const int i = i0 + r;
+                if (i < n_rho) p.F[(((size_t)m * p.batch_total + b) * 2 + c) * n_rho + i] = Fs[e];
+            }
         }
         __syncthreads();   // rings and Fs are refilled for the next block
     }
@@ -201,7 +230,7 @@ static int launch_kb_t(const KbParams& kp, int R, int nb, cudaStream_t st) {
     }
     KbParams& k = const_cast<KbParams&>(kp);
     k.nb = nb;
-    const long long items = (long long)((kp.n_rho + R - 1) / R) * nb;
+    const long long items = (long long)(kp.Fblk ? kp.n_chunks * (64 / R) : (kp.n_rho + R - 1) / R) * nb;
     const int grid = (int)std::min<long long>(items, (long long)per_sm * num_sms(dev));
     k_ring_spectra<LOGN, MODE><<<grid, R * 32, smem, st>>>(kp);
     ZM_LAUNCH_CHECK("k_ring_spectra");
@@ -338,9 +367,12 @@ static int pick_rings(zm_plan_t p, int batch) {
 // Fused gather kernel on images [b0, b0 + nb) (any alignment): writes F and,
 // when fhat_out is set, the polar samples.
 static int launch_gather(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int batch, float* F, float* fhat_out,
-                         bool resample_only, cudaStream_t st) {
-    const int R = pick_rings(p, batch);
+                         bool resample_only, uint8_t* Fblk, cudaStream_t st) {
+    const int R = Fblk ? 8 : pick_rings(p, batch);
     static thread_local KbParams kp;
+    kp.Fblk = resample_only ? nullptr : Fblk;
+    kp.fblk_half = fblk_half_bytes(p->n_max, p->n_chunks, 2 * batch);
+    kp.n_chunks = p->n_chunks;
     kp.n_rho = p->n_rho;
     kp.n_max = p->n_max;
     kp.batch_total = batch;
@@ -363,9 +395,13 @@ static int launch_gather(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, in
 
 // Ring FFT of given polar samples fhat[b][i][k] -> F for images [b0, b0 + nb)
 // of a batch of `batch`.
-static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int batch, float* F, cudaStream_t st) {
-    const int R = pick_rings(p, batch);
+static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int batch, float* F, uint8_t* Fblk,
+                            cudaStream_t st) {
+    const int R = Fblk ? 8 : pick_rings(p, batch);
     static thread_local KbParams kp;
+    kp.Fblk = Fblk;
+    kp.fblk_half = fblk_half_bytes(p->n_max, p->n_chunks, 2 * batch);
+    kp.n_chunks = p->n_chunks;
     kp.n_rho = p->n_rho;
     kp.n_max = p->n_max;
     kp.batch_total = batch;
@@ -389,8 +425,8 @@ static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int 
 // polar buffer (the caller's fhat_out, else the plan workspace) and then the
 // ring FFT; runs of other images take the fused gather kernel.
 int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* F,
-                   float* fhat_out, bool resample_only, cudaStream_t st) {
-    if (fhat_in) return launch_polar_fft(p, fhat_in, 0, batch, batch, F, st);
+                   float* fhat_out, bool resample_only, cudaStream_t st, uint8_t* Fblk) {
+    if (fhat_in) return launch_polar_fft(p, fhat_in, 0, batch, batch, F, Fblk, st);
     auto use_tma = [&](int b) { return !p->tune_gather && tma_eligible(imgs[b]); };
     bool any_tma = false;
     for (int b = 0; b < batch && !any_tma; ++b) any_tma = use_tma(b);
@@ -407,10 +443,10 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
         if (use_tma(b)) {
             while (e < batch && use_tma(e) && same_geometry(imgs[b], imgs[e])) ++e;
             s = launch_resample_tiles(p, imgs, b, e - b, fh, st);
-            if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, st);
+            if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, Fblk, st);
         } else {
             while (e < batch && !use_tma(e)) ++e;
-            s = launch_gather(p, imgs, b, e - b, batch, F, fhat_out, resample_only, st);
+            s = launch_gather(p, imgs, b, e - b, batch, F, fhat_out, resample_only, Fblk, st);
         }
         if (s != ZM_OK) return s;
         b = e;
@@ -421,6 +457,26 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
 int launch_projection(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, cudaStream_t st) {
     if (p->prec == PREC_FP32) return launch_projection_fp32(p, F, batch, out, flags, st);
     return launch_projection_tc(p, F, batch, out, flags, st);
+}
+
+int launch_moments(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* out,
+                   float* fhat_out, unsigned flags, cudaStream_t st) {
+    if (blocked_projection(p)) {
+        // spectra straight into bf16 operand blocks, then the blocked projection
+        const size_t half = fblk_half_bytes(p->n_max, p->n_chunks, 2 * batch);
+        int s = p->ws_Fblk.grow(2 * half);
+        if (s != ZM_OK) return s;
+        uint8_t* Fb = (uint8_t*)p->ws_Fblk.ptr;
+        s = launch_spectra(p, imgs, fhat_in, batch, nullptr, fhat_out, false, st, Fb);
+        if (s != ZM_OK) return s;
+        return launch_projection_blocked(p, Fb, batch, out, flags, st);
+    }
+    int s = p->ws_F.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
+    if (s != ZM_OK) return s;
+    float* F = (float*)p->ws_F.ptr;
+    s = launch_spectra(p, imgs, fhat_in, batch, F, fhat_out, false, st);
+    if (s != ZM_OK) return s;
+    return launch_projection(p, F, batch, out, flags, st);
 }
 
 }  // namespace zm
@@ -439,12 +495,7 @@ static int moments_common(zm_plan_t plan, const zm_image_t* imgs, const float* f
     }
     DeviceGuard g(plan->device);
     if (!g.ok) return set_error(ZM_ECUDA, "cannot select device %d", plan->device);
-    int s = plan->ws_F.grow(sizeof(float) * (size_t)(plan->n_max + 1) * batch * 2 * plan->n_rho);
-    if (s != ZM_OK) return s;
-    float* F = (float*)plan->ws_F.ptr;
-    s = launch_spectra(plan, imgs, fhat_in, batch, F, fhat_out, false, (cudaStream_t)stream);
-    if (s != ZM_OK) return s;
-    return launch_projection(plan, F, batch, out, flags, (cudaStream_t)stream);
+    return launch_moments(plan, imgs, fhat_in, batch, out, fhat_out, flags, (cudaStream_t)stream);
 }
 
 extern "C" int zm_moments(zm_plan_t plan, const zm_image_t* imgs, int batch, float* out, unsigned flags,
@@ -508,5 +559,7 @@ extern "C" int zm_plan_reserve(zm_plan_t plan, int batch) {
     const size_t rec = std::max<size_t>(64, (size_t)(plan->n_rho + 7) / 8);
     if (s == ZM_OK) s = plan->ws_red.grow(sizeof(double) * nb * rec * 4);
     if (s == ZM_OK) s = plan->ws_scale.grow(sizeof(float) * 2 * nb);
+    if (s == ZM_OK && blocked_projection(plan))
+        s = plan->ws_Fblk.grow(2 * fblk_half_bytes(plan->n_max, plan->n_chunks, 2 * batch));
     return s;
 }

@@ -380,7 +380,7 @@ int build_plan_tables(zm_plan_t p) {
                          p->R32m, p->Ahi, p->Alo, p->prec, a_scale);
     ZM_LAUNCH_CHECK("k_derive");
     ZM_CUDA_TRY(cudaDeviceSynchronize());
-    return ZM_OK;
+    return build_tc_blocks(p);
 }
 
 static void free_plan(zm_plan_t p) {
@@ -391,6 +391,8 @@ static void free_plan(zm_plan_t p) {
     cudaFree(p->R32m);
     cudaFree(p->Ahi);
     cudaFree(p->Alo);
+    cudaFree(p->Ablk);
+    cudaFree(p->ablk_off);
     cudaFree(p->tw);
     cudaFree(p->cs);
     cudaFree(p->mrow);

@@ -402,4 +402,273 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
     return ZM_OK;
 }
 
+// ============================================================== blocked form
+// The same contraction with the roles of the operands swapped and no
+// register work in the main loop: one CTA per (m, column tile) computes
+//   D[n][col] = sum_i A_m[n][i] F_m[col][i]
+// over the whole radial range (no split, no partial sums).  A (the MMA's M
+// side, K_m <= 128 rows) comes from the plan's operand blocks, F (the N side,
+// up to 256 columns) from blocks the ring-FFT kernel wrote, both already in
+// the canonical layout, so each 64-node chunk is four bulk copies into a ring
+// of shared-memory stages; one thread waits for a stage, issues its 4 x 3
+// MMAs and commits them to the stage's "empty" barrier, and refills the stage
+// of the previous chunk once those MMAs have read it.  The epilogue writes
+// the moments (Neumann factor applied) straight into out[b][idx(n, m)].
+constexpr int BLK_A_BYTES = 16 * 1024;        // A region of a stage: 128 rows x 64 k x 2 B
+
+struct BlkParams {
+    const uint8_t* Ablk;
+    const long long* ablk_off;
+    long long ablk_half;
+    const uint8_t* Fblk;
+    long long fblk_half;
+    float* out;
+    int* status;
+    int n_max, n_chunks, ncol, P;
+    int stages, stage_bytes, b_bytes;   // b_bytes: B region of one half in a stage
+    int neumann;
+    float inv_scale;
+};
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constant__ BlkParams p) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t full[8];
+    __shared__ __align__(8) uint64_t empty[8];
+    __shared__ uint32_t tslot;
+    __shared__ int okflag;
+    const int m = blockIdx.x, t = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Km = (p.n_max - m) / 2 + 1;
+    const int rg = (Km + 7) / 8;
+    const int cg = (p.ncol + 7) / 8;
+    const int cg0 = t * 32, cgt = min(32, cg - cg0);
+    const int cols_t = min(256, p.ncol - t * 256);
+    const int NT = ((cols_t + 15) / 16) * 16;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)NT) ncols <<= 1;
+    const int S = p.stages, nch = p.n_chunks;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[k])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[k])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        okflag = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tslot;
+    const uint32_t sm0 = smem_u32(sm);
+
+    if (tid == 0) {
+        const uint8_t* a_src = p.Ablk + p.ablk_off[m];
+        const size_t a_chunk = (size_t)rg * 1024;
+        const uint8_t* f_src = p.Fblk + (((size_t)m * nch) * cg + cg0) * 1024;
+        const size_t f_chunk = (size_t)cg * 1024;
+        const uint32_t tx = (uint32_t)(2 * (rg + cgt) * 1024);
+        auto load = [&](int c) {
+            const int st = c % S;
+            const uint32_t base = sm0 + (uint32_t)st * p.stage_bytes;
+            const uint32_t bar = smem_u32(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+            bulk_copy(base, a_src + c * a_chunk, (uint32_t)a_chunk, bar);
+            bulk_copy(base + BLK_A_BYTES, a_src + p.ablk_half + c * a_chunk, (uint32_t)a_chunk, bar);
+            bulk_copy(base + 2 * BLK_A_BYTES, f_src + c * f_chunk, (uint32_t)cgt * 1024, bar);
+            bulk_copy(base + 2 * BLK_A_BYTES + p.b_bytes, f_src + p.fblk_half + c * f_chunk, (uint32_t)cgt * 1024,
+                      bar);
+        };
+        const uint32_t idesc = instr_desc(NT, 0);
+        const unsigned long long t0 = global_ns();
+        int loaded = 0, done = 0;
+        bool ok = true;
+        for (; loaded < nch && loaded < S; ++loaded) load(loaded);
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c % S;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c / S) & 1), t0)) {
+                ok = false;
+                break;
+            }
+            const uint32_t base = sm0 + (uint32_t)st * p.stage_bytes;
+            const uint32_t ah = base, al = base + BLK_A_BYTES;
+            const uint32_t fh = base + 2 * BLK_A_BYTES, fl = fh + p.b_bytes;
+#pragma unroll
+            for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                const uint32_t off = ks * 256;      // 16 k = two core matrices along K
+                const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
+                const uint64_t dfh = smem_desc(fh + off), dfl = smem_desc(fl + off);
+                const uint32_t acc0 = (c == 0 && ks == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                    "l"(dah), "l"(dfh), "r"(idesc), "r"(acc0));
+                asm volatile(
+                    "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                    "l"(dah), "l"(dfl), "r"(idesc), "r"(1u));
+                asm volatile(
+                    "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                    "l"(dal), "l"(dfh), "r"(idesc), "r"(1u));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[st]))
+                         : "memory");
+            done = c + 1;
+            // refill the stage of the previous chunk once its MMAs have read it
+            if (c >= 1 && loaded < nch) {
+                const int pc = c - 1, ps = pc % S;
+                if (!mbar_wait(smem_u32(&empty[ps]), (uint32_t)((pc / S) & 1), t0)) {
+                    ok = false;
+                    break;
+                }
+                load(loaded++);
+            }
+        }
+        if (ok) ok = mbar_wait(smem_u32(&empty[(nch - 1) % S]), (uint32_t)(((nch - 1) / S) & 1), t0);
+        if (!ok) {
+            // a wait ran out: report it, then give the copies and MMAs in flight a
+            // bounded time to land before the shared memory and TMEM are released
+            atomicExch(p.status, ZM_ETIMEOUT);
+            const unsigned long long t1 = global_ns();
+            for (int c = done; c < loaded; ++c) mbar_wait(smem_u32(&full[c % S]), (uint32_t)((c / S) & 1), t1);
+            if (done > 0) mbar_wait(smem_u32(&empty[(done - 1) % S]), (uint32_t)(((done - 1) / S) & 1), t1);
+            okflag = 0;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // epilogue: TMEM lane = row n_local of D (warp w owns lanes 32w..32w+31)
+    if (okflag && warp * 32 < Km) {
+        const int nl = warp * 32 + lane;
+        const bool live = nl < Km;
+        const int idx = live ? moment_index(m + 2 * nl, m) : 0;
+        const float f = p.inv_scale * ((p.neumann && m == 0) ? 0.5f : 1.f);
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (live) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = t * 256 + c0 + j;
+                    if (c0 + j < cols_t) p.out[((size_t)(col >> 1) * p.P + idx) * 2 + (col & 1)] = __uint_as_float(r[j]) * f;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    }
+}
+
+// A halves -> operand blocks: row r < ceil(K_m/8)*8 of order m, chunk c;
+// rows past K_m and nodes past n_rho are zero.
+__global__ void k_build_ablk(const uint16_t* __restrict__ Ahi, const uint16_t* __restrict__ Alo,
+                             const int* __restrict__ mrow, const long long* __restrict__ ablk_off, long long half,
+                             int n_max, int n_rho, uint8_t* __restrict__ Ablk) {
+    const int m = blockIdx.x, c = blockIdx.y;
+    const int Km = (n_max - m) / 2 + 1, rg = (Km + 7) / 8;
+    for (int task = threadIdx.x; task < rg * 8 * 8; task += blockDim.x) {
+        const int row = task >> 3, kg = task & 7;
+        uint16_t h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = c * TC_KC + kg * 8 + e;
+            const bool on = row < Km && i < n_rho;
+            const size_t src = (size_t)(mrow[m] + row) * n_rho + i;
+            h[e] = on ? Ahi[src] : (uint16_t)0;
+            l[e] = on ? Alo[src] : (uint16_t)0;
+        }
+        const size_t o = ablk_off[m] + (size_t)c * rg * 1024 + (size_t)(row >> 3) * 1024 + kg * 128 + (row & 7) * 16;
+        uint4 vh, vl;
+        vh.x = h[0] | ((uint32_t)h[1] << 16); vh.y = h[2] | ((uint32_t)h[3] << 16);
+        vh.z = h[4] | ((uint32_t)h[5] << 16); vh.w = h[6] | ((uint32_t)h[7] << 16);
+        vl.x = l[0] | ((uint32_t)l[1] << 16); vl.y = l[2] | ((uint32_t)l[3] << 16);
+        vl.z = l[4] | ((uint32_t)l[5] << 16); vl.w = l[6] | ((uint32_t)l[7] << 16);
+        *reinterpret_cast<uint4*>(Ablk + o) = vh;
+        *reinterpret_cast<uint4*>(Ablk + half + o) = vl;
+    }
+}
+
+int build_tc_blocks(zm_plan_t p) {
+    p->n_chunks = (p->n_rho + TC_KC - 1) / TC_KC;
+    if (p->prec != PREC_BF16X3 || p->n_max / 2 + 1 > TC_M) return ZM_OK;   // blocked form not used
+    p->ablk_off_h.assign(p->n_max + 2, 0);
+    for (int m = 0; m <= p->n_max; ++m) {
+        const int rg = ((p->n_max - m) / 2 + 1 + 7) / 8;
+        p->ablk_off_h[m + 1] = p->ablk_off_h[m] + (long long)p->n_chunks * rg * 1024;
+    }
+    p->ablk_half = p->ablk_off_h[p->n_max + 1];
+    ZM_CUDA_TRY(cudaMalloc(&p->Ablk, 2 * (size_t)p->ablk_half));
+    ZM_CUDA_TRY(cudaMalloc(&p->ablk_off, sizeof(long long) * (p->n_max + 2)));
+    ZM_CUDA_TRY(cudaMemcpy(p->ablk_off, p->ablk_off_h.data(), sizeof(long long) * (p->n_max + 2),
+                           cudaMemcpyHostToDevice));
+    k_build_ablk<<<dim3(p->n_max + 1, p->n_chunks), 256>>>(p->Ahi, p->Alo, p->mrow, p->ablk_off, p->ablk_half,
+                                                           p->n_max, p->n_rho, p->Ablk);
+    ZM_LAUNCH_CHECK("k_build_ablk");
+    ZM_CUDA_TRY(cudaDeviceSynchronize());
+    return ZM_OK;
+}
+
+bool blocked_projection(zm_plan_t p) { return p->Ablk != nullptr; }
+
+int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float* out, unsigned flags,
+                              cudaStream_t st) {
+    const int ncol = 2 * batch;
+    const int tiles = (ncol + 255) / 256;
+    const int nt_max = ((std::min(ncol, 256) + 15) / 16) * 16;
+    BlkParams bp;
+    bp.Ablk = p->Ablk;
+    bp.ablk_off = p->ablk_off;
+    bp.ablk_half = p->ablk_half;
+    bp.Fblk = Fblk;
+    bp.fblk_half = (long long)fblk_half_bytes(p->n_max, p->n_chunks, ncol);
+    bp.out = out;
+    bp.status = p->status;
+    bp.n_max = p->n_max;
+    bp.n_chunks = p->n_chunks;
+    bp.ncol = ncol;
+    bp.P = p->P;
+    bp.b_bytes = (nt_max / 8) * 1024;
+    bp.stage_bytes = 2 * BLK_A_BYTES + 2 * bp.b_bytes;
+    const int cap = 200 * 1024;
+    bp.stages = std::max(2, std::min(8, cap / bp.stage_bytes));
+    bp.neumann = (flags & ZM_NEUMANN) ? 1 : 0;
+    bp.inv_scale = 1.0f / p->a_scale;
+    const size_t smem = (size_t)bp.stages * bp.stage_bytes;
+    static size_t configured[64] = {0};
+    const int dev = p->device;
+    if (dev >= 64 || smem > configured[dev]) {
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_project_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev < 64) configured[dev] = smem;
+    }
+    k_project_blk<<<dim3(p->n_max + 1, tiles), TC_THREADS, smem, st>>>(bp);
+    ZM_LAUNCH_CHECK("k_project_blk");
+    return ZM_OK;
+}
+
 }  // namespace zm

@@ -151,9 +151,7 @@ static int launch_group(zm_server_t s, SrvGroup& g, cudaStream_t st) {
     }
     zm_plan_t p = g.gp->plan;
     const int P = num_moments(g.gp->n_max);
-    float* F = (float*)p->ws_F.ptr;
-    int rc = launch_spectra(p, imgs.data(), nullptr, gb, F, nullptr, false, st);
-    if (rc == ZM_OK) rc = launch_projection(p, F, gb, g.gp->out, g.reqs[0].flags, st);
+    const int rc = launch_moments(p, imgs.data(), nullptr, gb, g.gp->out, nullptr, g.reqs[0].flags, st);
     if (rc != ZM_OK) return rc;
     for (int j = 0; j < gb; ++j) {
         const SrvRequest& r = g.reqs[j];

@@ -101,6 +101,16 @@ struct zm_plan_s {
     int* mrow = nullptr;        // [n_max + 2] first m-major row of each m
     int2* pair_nm = nullptr;    // [P] (n, m) of each moment index
     std::vector<int> mrow_h;
+    // bf16 plans with K_m <= 128: the A halves as tensor-core operand blocks,
+    // chunk by chunk of 64 radial nodes, each chunk in the canonical K-major
+    // core-matrix layout (8 rows x 16 B; 8-row groups 1 KB apart), so that one
+    // bulk copy moves a chunk into shared memory.  Half h, order m, chunk c:
+    // Ablk + h * ablk_half + ablk_off_h[m] + c * ceil(K_m / 8) KB.
+    uint8_t* Ablk = nullptr;
+    std::vector<long long> ablk_off_h;
+    long long* ablk_off = nullptr;   // device copy of ablk_off_h
+    long long ablk_half = 0;
+    int n_chunks = 0;                // ceil(n_rho / 64)
     // workspace (grown on demand)
     zm::Workspace ws_F;         // ring spectra F[m][b][2][n_rho] (fp32)
     zm::Workspace ws_fhat;      // polar samples f[b][i][k] (fp32)
@@ -109,6 +119,7 @@ struct zm_plan_s {
     zm::Workspace ws_red;       // reduction partials
     zm::Workspace ws_scale;     // per-image min / max (normalisation)
     zm::Workspace ws_colmax;    // per-column max |F| (fp16 split scaling)
+    zm::Workspace ws_Fblk;      // ring spectra as bf16 hi / lo operand blocks (blocked projection)
     int* status = nullptr;      // device status word: ZM_ETIMEOUT after a timed-out wait
     // launch choices
     int kb_rings = 8;           // rings per CTA in the resample + FFT kernel
@@ -121,10 +132,30 @@ struct zm_plan_s {
 namespace zm {
 
 // ---------------------------------------------------------------- launchers
+// Fblk: write the spectra as bf16 operand blocks instead of F (see fblk_row).
 int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch,
-                   float* F, float* fhat_out, bool resample_only, cudaStream_t st);
+                   float* F, float* fhat_out, bool resample_only, cudaStream_t st, uint8_t* Fblk = nullptr);
 int launch_projection(zm_plan_t p, const float* F, int batch, float* out, unsigned flags,
                       cudaStream_t st);
+// Moments of a batch (images, or polar samples when fhat_in is set): ring
+// spectra, then the projection; bf16 plans take the blocked tensor-core path.
+int launch_moments(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* out,
+                   float* fhat_out, unsigned flags, cudaStream_t st);
+// Blocked tensor-core projection (project_tc.cu).
+int build_tc_blocks(zm_plan_t p);
+bool blocked_projection(zm_plan_t p);
+int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float* out, unsigned flags,
+                              cudaStream_t st);
+
+// Layout of the spectra blocks: half-size in bytes, and the byte offset of the
+// 16-byte row holding F[m][col][i .. i+7] (i a multiple of 8) within a half.
+__host__ __device__ inline size_t fblk_half_bytes(int n_max, int n_chunks, int ncol) {
+    return (size_t)(n_max + 1) * n_chunks * ((ncol + 7) / 8) * 1024;
+}
+__host__ __device__ inline size_t fblk_row(int m, int i, int col, int n_chunks, int ncol) {
+    const int cg = (ncol + 7) / 8;
+    return ((((size_t)m * n_chunks + (i >> 6)) * cg + (col >> 3)) << 10) + (((i & 63) >> 3) << 7) + ((col & 7) << 4);
+}
 void count_launch(int n = 1);
 int launch_reconstruct(zm_plan_t p, const float* moments, int batch, float* out,
                        unsigned flags, cudaStream_t st);
