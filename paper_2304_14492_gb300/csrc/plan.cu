@@ -380,7 +380,8 @@ int build_plan_tables(zm_plan_t p) {
                          p->R32m, p->Ahi, p->Alo, p->prec, a_scale);
     ZM_LAUNCH_CHECK("k_derive");
     ZM_CUDA_TRY(cudaDeviceSynchronize());
-    return build_tc_blocks(p);
+    const int s = build_tc_blocks(p);
+    return s != ZM_OK ? s : build_recon_blocks(p);
 }
 
 static void free_plan(zm_plan_t p) {
@@ -393,6 +394,8 @@ static void free_plan(zm_plan_t p) {
     cudaFree(p->Alo);
     cudaFree(p->Ablk);
     cudaFree(p->ablk_off);
+    cudaFree(p->Rblk);
+    cudaFree(p->rblk_off);
     cudaFree(p->tw);
     cudaFree(p->cs);
     cudaFree(p->mrow);

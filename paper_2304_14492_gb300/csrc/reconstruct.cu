@@ -274,6 +274,10 @@ static int launch_radial(zm_plan_t p, const float* moments, int batch, unsigned 
     const int s = p->ws_G.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
     if (s != ZM_OK) return s;
     float* G = (float*)p->ws_G.ptr;
+    if (p->Rblk) {
+        *G_out = G;
+        return launch_radial_tc(p, moments, batch, flags, G, st);
+    }
     const size_t smem = sizeof(float2) * RB * (size_t)(p->n_max / 2 + 1);
     int dev = p->device;
     static size_t configured[64] = {0};

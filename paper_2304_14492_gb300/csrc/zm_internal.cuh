@@ -111,6 +111,14 @@ struct zm_plan_s {
     long long* ablk_off = nullptr;   // device copy of ablk_off_h
     long long ablk_half = 0;
     int n_chunks = 0;                // ceil(n_rho / 64)
+    // bf16 plans: R (reconstruction) split into hi / lo operand blocks, one per
+    // (m, 128-ring tile, 64-order chunk); half h of order m starts at
+    // Rblk + h * rblk_half + rblk_off_h[m]
+    uint8_t* Rblk = nullptr;
+    std::vector<long long> rblk_off_h;
+    long long* rblk_off = nullptr;
+    long long rblk_half = 0;
+    int n_rtiles = 0;
     // workspace (grown on demand)
     zm::Workspace ws_F;         // ring spectra F[m][b][2][n_rho] (fp32)
     zm::Workspace ws_fhat;      // polar samples f[b][i][k] (fp32)
@@ -146,6 +154,9 @@ int build_tc_blocks(zm_plan_t p);
 bool blocked_projection(zm_plan_t p);
 int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float* out, unsigned flags,
                               cudaStream_t st);
+// Tensor-core radial reconstruction (recon_tc.cu), bf16 plans.
+int build_recon_blocks(zm_plan_t p);
+int launch_radial_tc(zm_plan_t p, const float* moments, int batch, unsigned flags, float* G, cudaStream_t st);
 
 // Layout of the spectra blocks: half-size in bytes, and the byte offset of the
 // 16-byte row holding F[m][col][i .. i+7] (i a multiple of 8) within a half.
