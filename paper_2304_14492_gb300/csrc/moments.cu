@@ -93,7 +93,30 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
     // with operand blocks, ring blocks run up to the last 64-node chunk (rings
     // past n_rho are zero), so that every block of the chunk is written
     const int n_rb = p.Fblk ? p.n_chunks * (64 / R) : (n_rho + R - 1) / R;
-    for (int item = blockIdx.x; item < n_rb * p.nb; item += gridDim.x) {
+    const int n_items = n_rb * p.nb;
+    // polar input: this warp's ring of a ring block straight into the FFT
+    // registers (lane t holds z[t + L s]); the next block's ring is loaded as
+    // soon as the current FFT has left the registers
+    float2 v[FFT::Q];
+    auto load_ring = [&](int item) {
+        const int bl = item / n_rb;
+        const int i = (item - bl * n_rb) * R + warp;
+        const bool live = lane < FFT::L && i < n_rho;
+        const float* src = p.fhat_in + ((size_t)(p.b_off + bl) * n_rho + (live ? i : 0)) * N;
+        if ((reinterpret_cast<uintptr_t>(p.fhat_in) & 7) == 0) {
+            const float2* z = reinterpret_cast<const float2*>(src);
+#pragma unroll
+            for (int s = 0; s < FFT::Q; ++s) v[s] = live ? __ldg(&z[lane + FFT::L * s]) : make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int s = 0; s < FFT::Q; ++s) {
+                const int j = lane + FFT::L * s;
+                v[s] = live ? make_float2(__ldg(src + 2 * j), __ldg(src + 2 * j + 1)) : make_float2(0.f, 0.f);
+            }
+        }
+    };
+    if (MODE == KB_POLAR && (int)blockIdx.x < n_items) load_ring(blockIdx.x);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int bl = item / n_rb;
         const int i0 = (item - bl * n_rb) * R;
         const int b = p.b_off + bl;
@@ -103,14 +126,14 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
             for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
                 const int r = idx >> LOGN, k = idx & (N - 1);
                 const int i = i0 + r;
-                float v = 0.f;
+                float vv = 0.f;
                 if (i < n_rho) {
                     const float rad = im.r * __ldg(&p.rho32[i]);
                     const float2 c = __ldg(&p.cs[k]);
-                    v = bilinear(im, fmaf(rad, c.x, im.cx), fmaf(-rad, c.y, im.cy));
-                    if (p.fhat_out) p.fhat_out[((size_t)b * n_rho + i) * N + k] = v;
+                    vv = bilinear(im, fmaf(rad, c.x, im.cx), fmaf(-rad, c.y, im.cy));
+                    if (p.fhat_out) p.fhat_out[((size_t)b * n_rho + i) * N + k] = vv;
                 }
-                if (MODE != KB_RESAMPLE) rings[r * ROW + k] = v;
+                if (MODE != KB_RESAMPLE) rings[r * ROW + k] = vv;
             }
         }
         if (MODE == KB_RESAMPLE) continue;
@@ -118,24 +141,7 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
 
         {
             float* row = rings + warp * ROW;
-            float2 v[FFT::Q];
-            if (MODE == KB_POLAR) {
-                const int i = i0 + warp;
-                const bool live = lane < FFT::L && i < n_rho;
-                const float* src = p.fhat_in + ((size_t)b * n_rho + (live ? i : 0)) * N;
-                if ((reinterpret_cast<uintptr_t>(p.fhat_in) & 7) == 0) {
-                    const float2* z = reinterpret_cast<const float2*>(src);
-#pragma unroll
-                    for (int s = 0; s < FFT::Q; ++s)
-                        v[s] = live ? __ldg(&z[lane + FFT::L * s]) : make_float2(0.f, 0.f);
-                } else {
-#pragma unroll
-                    for (int s = 0; s < FFT::Q; ++s) {
-                        const int j = lane + FFT::L * s;
-                        v[s] = live ? make_float2(__ldg(src + 2 * j), __ldg(src + 2 * j + 1)) : make_float2(0.f, 0.f);
-                    }
-                }
-            } else {
+            if (MODE != KB_POLAR) {
                 const float2* z = reinterpret_cast<const float2*>(row);
 #pragma unroll
                 for (int s = 0; s < FFT::Q; ++s)
@@ -149,6 +155,7 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
                 for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::fwd_index(r, lane))] = v[r];
             }
             __syncwarp();
+            if (MODE == KB_POLAR && item + (int)gridDim.x < n_items) load_ring(item + gridDim.x);
             for (int m = lane; m <= n_max; m += 32) {
                 const float2 A = X[FFT::pad(m)];
                 const float2 B = cconj(X[FFT::pad((FFT::M - m) & (FFT::M - 1))]);

@@ -148,7 +148,30 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
         if (i < n_rho && lane < L) {
             const size_t row = ((size_t)b * n_rho + i) * N;
             float2* o = out ? reinterpret_cast<float2*>(out + row) : nullptr;
-            if (ERR) {
+            if (ERR && FFT::TBUF >= Q * 32) {
+                // f~ goes out and into this warp's transpose buffer (free after
+                // the inverse FFT), so that all Q reference loads can be in
+                // flight at once without holding f~ in registers
+                const float2* rf = reinterpret_cast<const float2*>(ref + row);
+#pragma unroll
+                for (int r = 0; r < Q; ++r) {
+                    const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
+                    if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
+                    tbuf[r * 32 + lane] = x;
+                }
+                float2 f[Q];
+#pragma unroll
+                for (int r = 0; r < Q; ++r) f[r] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r)]);
+#pragma unroll
+                for (int r = 0; r < Q; ++r) {
+                    const float2 x = tbuf[r * 32 + lane];
+                    const float d0 = f[r].x - x.x, d1 = f[r].y - x.y;
+                    sd = fmaf(d0, d0, fmaf(d1, d1, sd));
+                    sf = fmaf(f[r].x, f[r].x, fmaf(f[r].y, f[r].y, sf));
+                    mx = fmaxf(mx, fmaxf(f[r].x, f[r].y));
+                    cnt += 2.f;
+                }
+            } else if (ERR) {
                 const float2* rf = reinterpret_cast<const float2*>(ref + row);
                 // groups of four loads in flight, consumed as they arrive (few live registers)
 #pragma unroll
