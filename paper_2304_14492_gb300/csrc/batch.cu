@@ -7,7 +7,9 @@
 // on the plan's n_max).  A group runs the ordinary path (resampling, ring FFT,
 // projection into a group buffer); one small kernel then copies every
 // request's prefix into its own output.  The whole sequence is captured once
-// into a CUDA graph and replayed while the request pointers stay the same.
+// into a CUDA graph and replayed while the request pointers stay the same;
+// the groups fork onto BATCH_BRANCHES side streams (balanced by pixel count),
+// so they become parallel branches of the graph and small groups overlap.
 // Launch choices per group come from a small autotuner (timed candidates,
 // cached in a JSON file).
 #include <algorithm>
@@ -37,10 +39,15 @@ struct BatchGroup {
     float* out_buf = nullptr;          // [members][P(n_max)][2]
 };
 
+constexpr int BATCH_BRANCHES = 4;      // side streams the groups fork onto
+
 }  // namespace zm
 
 struct zm_batch_s {
     int device = 0;
+    cudaStream_t side[zm::BATCH_BRANCHES] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[zm::BATCH_BRANCHES] = {};
+    std::vector<int> branch;           // side stream of each group
     unsigned plan_flags = 0;
     std::vector<zm_request_t> reqs;    // shapes (and pointers) at creation
     std::vector<zm::BatchGroup> groups;
@@ -89,6 +96,11 @@ static void free_batch(zm_batch_t b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < BATCH_BRANCHES; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->d_copy) cudaFree(b->d_copy);
     for (auto& g : b->groups) {
         if (g.out_buf) cudaFree(g.out_buf);
@@ -101,16 +113,25 @@ static void free_batch(zm_batch_t b) {
 
 namespace zm {
 
-// The whole batch on one stream: per group resampling + ring FFT + projection
-// into its buffer, then the prefix copies.
+// The whole batch from stream st: the groups fork onto the side streams (per
+// group resampling + ring FFT + projection into its buffer), join back on st,
+// then the prefix copies.
 static int enqueue_batch(zm_batch_t b, const zm_request_t* reqs, unsigned flags, cudaStream_t st) {
     std::vector<zm_image_t> imgs;
-    for (auto& g : b->groups) {
+    ZM_CUDA_TRY(cudaEventRecord(b->ev_fork, st));
+    for (int k = 0; k < BATCH_BRANCHES; ++k) ZM_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->ev_fork, 0));
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& g = b->groups[gi];
         imgs.clear();
         for (int r : g.members) imgs.push_back(reqs[r].image);
         const int gb = (int)g.members.size();
-        const int s = launch_moments(g.plan, imgs.data(), nullptr, gb, g.out_buf, nullptr, flags, st);
+        const int s = launch_moments(g.plan, imgs.data(), nullptr, gb, g.out_buf, nullptr, flags,
+                                     b->side[b->branch[gi]]);
         if (s != ZM_OK) return s;
+    }
+    for (int k = 0; k < BATCH_BRANCHES; ++k) {
+        ZM_CUDA_TRY(cudaEventRecord(b->ev_join[k], b->side[k]));
+        ZM_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_join[k], 0));
     }
     k_batch_copy<<<(unsigned)b->reqs.size(), 256, 0, st>>>(b->d_copy);
     ZM_LAUNCH_CHECK("k_batch_copy");
@@ -303,6 +324,32 @@ extern "C" int zm_batch_create(zm_batch_t* batch, const zm_request_t* reqs, int 
     }
     cudaError_t e = cudaMalloc(&b->d_copy, sizeof(CopyDesc) * count);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int k = 0; k < BATCH_BRANCHES && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    // branches: largest groups first onto the least-loaded side stream (load =
+    // pixels resampled + polar nodes transformed)
+    {
+        std::vector<std::pair<double, int>> cost;
+        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+            double c = 0;
+            for (int r : b->groups[gi].members)
+                c += (double)reqs[r].image.height * reqs[r].image.width + (double)reqs[r].n_rho * reqs[r].n_theta;
+            cost.push_back({c, (int)gi});
+        }
+        std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        double load[BATCH_BRANCHES] = {0};
+        b->branch.assign(b->groups.size(), 0);
+        for (auto& cg : cost) {
+            int k = 0;
+            for (int j = 1; j < BATCH_BRANCHES; ++j)
+                if (load[j] < load[k]) k = j;
+            b->branch[cg.second] = k;
+            load[k] += cg.first;
+        }
+    }
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_error(e, "batch set-up");
