@@ -568,6 +568,7 @@ def bench_serving(zm, rate=2000.0, seconds=10.0, seed=7):
             "max_ms": stats["max_ms"], "groups_launched": int(stats["groups_launched"]),
             "peak_device_bytes": int(stats["peak_bytes"]), "precision": "bf16x3",
             "alone_vs_mix": {"requests_rerun": rerun, "max_rel_diff": worst},
+            "host_direct": bool(stats["host_direct"]),
             "note": "statistics reset after 16 plan-warming requests; latency = submit -> moments in host memory"}
 
 

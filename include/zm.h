@@ -266,6 +266,10 @@ typedef struct {
     double p50_ms, p99_ms, max_ms;  /* latency: submit -> result on the host */
     double images_per_s;            /* completed / (last completion - first submit) */
     unsigned long long peak_bytes;  /* largest device footprint of requests in flight */
+    int host_direct;                /* 1: kernels read the host images and write the results
+                                       in place (the GPU reaches pageable host memory through
+                                       the host page tables); 0: copies through a pinned mirror
+                                       of the arena (also forced by ZM_SERVER_STAGING=1) */
 } zm_server_stats_t;
 
 /*
@@ -274,7 +278,9 @@ typedef struct {
  * budget (the arena is allocated once, here), groups the admitted ones by
  * polar grid (one plan per (n_rho, n_theta), order = the largest seen), and
  * launches each group on the stream bound to its grid: copy in, resampling,
- * ring FFT, projection, copy out.  Groups of different grids overlap on the
+ * ring FFT, projection, copy out (by kernels reading and writing the callers'
+ * host buffers where the GPU reaches pageable host memory through the host
+ * page tables, else through a pinned mirror of the arena).  Groups of different grids overlap on the
  * device; requests arriving meanwhile are admitted as memory frees up.
  * Plans (tables on the device) stay resident for the server's lifetime.
  */

@@ -4,14 +4,19 @@
 // waiting requests, in arrival order, while their device bytes fit a fixed
 // arena (the HBM budget, allocated once), groups the admitted ones by polar
 // grid, and launches each group on the stream bound to that grid: host->device
-// copy through a pinned mirror of the arena, resampling, ring FFT, projection,
-// device->host copy.  Groups of different grids run concurrently; requests
+// copy, resampling, ring FFT, projection, device->host copy.  Where the GPU
+// reads pageable host memory through the host page tables (GB300: NVLink-C2C
+// with ATS), a kernel gathers each host image straight into the arena and
+// scatters each result straight into the caller's `out`; elsewhere the copies
+// go through a pinned mirror of the arena.  Groups of different grids run
+// concurrently; requests
 // that arrive meanwhile are admitted as soon as earlier ones complete and free
 // their bytes.  Plans stay resident; a grid's plan is rebuilt only when a
 // request needs a larger order than any seen before for it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -25,6 +30,21 @@
 namespace zm {
 
 using Clock = std::chrono::steady_clock;
+
+// host image rows (any pitch, pageable memory the GPU reads through the host
+// page tables) -> packed rows in the device arena
+__global__ void k_host_rows_in(const float* __restrict__ src, long long pitch, int h, int w, float* __restrict__ dst) {
+    const long long n = (long long)h * w;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long y = e / w, x = e - y * w;
+        dst[e] = src[y * pitch + x];
+    }
+}
+
+// device result -> the caller's host buffer (pageable, through the host page tables)
+__global__ void k_host_out(const float* __restrict__ src, int n, float* __restrict__ dst) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) dst[e] = src[e];
+}
 
 struct SrvRequest {
     unsigned long long ticket = 0;
@@ -127,6 +147,7 @@ struct zm_server_s {
     std::vector<zm::SrvRequest> admitted;
     std::deque<zm::SrvGroup> inflight;
     std::vector<char> done;              // by ticket
+    bool host_direct = false;            // kernels read / write the callers' host buffers
     unsigned long long next_ticket = 1;
     zm_server_stats_t st{};
     std::vector<double> lat_ms;
@@ -143,11 +164,21 @@ static int launch_group(zm_server_t s, SrvGroup& g, cudaStream_t st) {
     std::vector<zm_image_t> imgs(gb);
     for (int j = 0; j < gb; ++j) {
         const SrvRequest& r = g.reqs[j];
-        // host image -> pinned mirror -> device arena (rows packed, pitch = width)
-        float* ph = reinterpret_cast<float*>(s->pinned + r.off);
-        for (int y = 0; y < r.h; ++y) memcpy(ph + (size_t)y * r.w, r.image + (size_t)y * r.pitch, sizeof(float) * r.w);
-        ZM_CUDA_TRY(cudaMemcpyAsync(s->dev + r.off, ph, r.img_bytes, cudaMemcpyHostToDevice, st));
-        imgs[j] = zm_image_t{reinterpret_cast<const float*>(s->dev + r.off), r.h, r.w, r.w, 0.f, 0.f, -1.f};
+        float* d = reinterpret_cast<float*>(s->dev + r.off);
+        if (s->host_direct) {
+            // the GPU gathers the host rows itself (no CPU copy)
+            const long long n = (long long)r.h * r.w;
+            const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+            k_host_rows_in<<<blocks, 256, 0, st>>>(r.image, r.pitch, r.h, r.w, d);
+            ZM_LAUNCH_CHECK("k_host_rows_in");
+        } else {
+            // host image -> pinned mirror -> device arena (rows packed, pitch = width)
+            float* ph = reinterpret_cast<float*>(s->pinned + r.off);
+            for (int y = 0; y < r.h; ++y)
+                memcpy(ph + (size_t)y * r.w, r.image + (size_t)y * r.pitch, sizeof(float) * r.w);
+            ZM_CUDA_TRY(cudaMemcpyAsync(d, ph, r.img_bytes, cudaMemcpyHostToDevice, st));
+        }
+        imgs[j] = zm_image_t{d, r.h, r.w, r.w, 0.f, 0.f, -1.f};
     }
     zm_plan_t p = g.gp->plan;
     const int P = num_moments(g.gp->n_max);
@@ -155,8 +186,14 @@ static int launch_group(zm_server_t s, SrvGroup& g, cudaStream_t st) {
     if (rc != ZM_OK) return rc;
     for (int j = 0; j < gb; ++j) {
         const SrvRequest& r = g.reqs[j];
-        ZM_CUDA_TRY(cudaMemcpyAsync(s->pinned + r.off + r.img_bytes, g.gp->out + (size_t)j * P * 2, r.out_bytes,
-                                    cudaMemcpyDeviceToHost, st));
+        const float* src = g.gp->out + (size_t)j * P * 2;
+        if (s->host_direct) {
+            const int n = (int)(r.out_bytes / sizeof(float));
+            k_host_out<<<(n + 255) / 256, 256, 0, st>>>(src, n, r.out);
+            ZM_LAUNCH_CHECK("k_host_out");
+        } else {
+            ZM_CUDA_TRY(cudaMemcpyAsync(s->pinned + r.off + r.img_bytes, src, r.out_bytes, cudaMemcpyDeviceToHost, st));
+        }
     }
     ZM_CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
     ZM_CUDA_TRY(cudaEventRecord(g.done, st));
@@ -201,7 +238,7 @@ static bool schedule_once(zm_server_t s) {
         if (q != cudaSuccess) s->error = cuda_error(q, "server group");
         const auto now = Clock::now();
         for (const SrvRequest& r : it->reqs) {
-            memcpy(r.out, s->pinned + r.off + r.img_bytes, r.out_bytes);
+            if (!s->host_direct) memcpy(r.out, s->pinned + r.off + r.img_bytes, r.out_bytes);
             s->arena.release(r.off, r.img_bytes + r.out_bytes);
             s->done[r.ticket] = 1;
             s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
@@ -314,10 +351,19 @@ extern "C" int zm_server_create(zm_server_t* server, const zm_server_config_t* c
     if (s->cfg.max_group <= 0) s->cfg.max_group = 64;
     int rc = ZM_OK;
     if (cudaGetDevice(&s->device) != cudaSuccess) rc = set_error(ZM_ECUDA, "no CUDA device");
+    if (rc == ZM_OK) {
+        // direct host access needs pageable memory reached through the host page
+        // tables; ZM_SERVER_STAGING=1 keeps the pinned-mirror copies anyway
+        int pageable = 0, host_tables = 0;
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, s->device);
+        cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, s->device);
+        const char* force = getenv("ZM_SERVER_STAGING");
+        s->host_direct = pageable && host_tables && !(force && force[0] == '1');
+    }
     const size_t n = Arena::round(s->cfg.hbm_budget);
     if (rc == ZM_OK) {
         cudaError_t e = cudaMalloc(&s->dev, n);
-        if (e == cudaSuccess) e = cudaHostAlloc(&s->pinned, n, cudaHostAllocDefault);
+        if (e == cudaSuccess && !s->host_direct) e = cudaHostAlloc(&s->pinned, n, cudaHostAllocDefault);
         for (int k = 0; k < s->cfg.streams && e == cudaSuccess; ++k) {
             cudaStream_t st;
             e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -421,6 +467,7 @@ extern "C" int zm_server_stats(zm_server_t s, zm_server_stats_t* out) {
     const double span = std::chrono::duration<double>(s->t_last - s->t_first).count();
     out->images_per_s = (span > 0 && s->st.completed) ? s->st.completed / span : 0.0;
     out->peak_bytes = s->arena.peak;
+    out->host_direct = s->host_direct ? 1 : 0;
     return ZM_OK;
 }
 

@@ -57,7 +57,7 @@ class zm_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
                 ("rejected", ctypes.c_ulonglong), ("groups_launched", ctypes.c_ulonglong),
                 ("p50_ms", c_double), ("p99_ms", c_double), ("max_ms", c_double),
-                ("images_per_s", c_double), ("peak_bytes", ctypes.c_ulonglong)]
+                ("images_per_s", c_double), ("peak_bytes", ctypes.c_ulonglong), ("host_direct", c_int)]
 
 
 # name -> (restype, argtypes); mirrors include/zm.h

@@ -177,3 +177,15 @@ def test_reset_stats_only_when_drained():
         assert st["completed"] == 0 and st["submitted"] == 0 and st["p99_ms"] == 0
     finally:
         zm.zm_server_destroy(srv, 10.0)
+
+
+def test_direct_host_access_and_pinned_staging_agree(monkeypatch):
+    """The two copy paths (kernels on the callers' host buffers where the GPU
+    reaches pageable host memory, else a pinned mirror) give identical results."""
+    reqs = make_requests(12, seed=5)
+    direct, st_d = run_server(reqs, 256 << 20)
+    monkeypatch.setenv("ZM_SERVER_STAGING", "1")
+    staged, st_s = run_server(reqs, 256 << 20)
+    assert st_s["host_direct"] == 0
+    for a, b in zip(direct, staged):
+        assert metrics.rel_max_err(a[:, 0] + 1j * a[:, 1], b[:, 0] + 1j * b[:, 1]) <= 1e-5
