@@ -1,0 +1,162 @@
+// Host frames -> device disk boxes (zm_upload_disk).
+//
+// Only the pixels a polar sample's bilinear stencil can touch are needed: the
+// bounding box of the disk, X in [cx - r, cx + r], Y in [cy - r, cy + r], plus
+// the stencil's right / lower neighbour and one pixel of margin for float
+// rounding.  A kernel reads those rows from host memory the GPU can reach
+// (pinned, or pageable where the device walks the host page tables) and packs
+// them into a device buffer; the returned descriptors carry the shifted
+// geometry.  At 4K (3840x2160, disk of diameter 2160) that is 18.7 MB of the
+// frame's 33.2 MB.
+#include <algorithm>
+#include <cmath>
+
+#include "zm_internal.cuh"
+
+namespace zm {
+
+constexpr int UP_MAX_IMG = 64;
+
+struct UpBox {
+    const float* src;     // host row 0, column 0 of the box (device-usable address)
+    long long spitch;     // host pitch (elements)
+    int w, h;             // box size
+    long long dst;        // offset of the box in the device buffer (floats)
+    int dpitch;           // device pitch (elements, multiple of 4)
+};
+
+struct UpParams {
+    float* dev;
+    int n;
+    UpBox box[UP_MAX_IMG];
+};
+
+// blockIdx.y = box, blockIdx.x strides rows.  Rows whose host start is 16-byte
+// aligned (and pitch a multiple of 4) move as float4 with four loads in flight
+// per thread: the host link has a long latency, so many bytes must be in
+// flight; other rows take the scalar loop.
+__global__ void __launch_bounds__(256) k_upload_boxes(const __grid_constant__ UpParams p) {
+    const UpBox bx = p.box[blockIdx.y];
+    const bool vec = ((reinterpret_cast<uintptr_t>(bx.src) & 15u) == 0) && (bx.spitch & 3) == 0;
+    for (int y = blockIdx.x; y < bx.h; y += gridDim.x) {
+        const float* s = bx.src + (long long)y * bx.spitch;
+        float* d = p.dev + bx.dst + (long long)y * bx.dpitch;
+        if (vec) {
+            const int n4 = bx.w >> 2;
+            const float4* s4 = reinterpret_cast<const float4*>(s);
+            float4* d4 = reinterpret_cast<float4*>(d);
+            for (int x0 = threadIdx.x; x0 < n4; x0 += 4 * blockDim.x) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int x = x0 + u * blockDim.x;
+                    if (x < n4) v[u] = s4[x];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int x = x0 + u * blockDim.x;
+                    if (x < n4) d4[x] = v[u];
+                }
+            }
+            for (int x = (n4 << 2) + threadIdx.x; x < bx.w; x += blockDim.x) d[x] = s[x];
+        } else {
+            for (int x = threadIdx.x; x < bx.w; x += blockDim.x) d[x] = s[x];
+        }
+    }
+}
+
+struct Box {
+    int x0, y0, w, h, pitch;
+};
+
+// the box of image im (geometry resolved), clipped to the image
+static Box disk_box(const zm_image_t& im) {
+    const GeoImage g = resolve(im);
+    // left edge rounded down to a multiple of 4 columns: box rows of a 16-byte
+    // aligned frame then start 16-byte aligned (vector loads)
+    const int x0 = std::max(0, (int)std::floor(g.cx - g.r) - 1) & ~3;
+    const int y0 = std::max(0, (int)std::floor(g.cy - g.r) - 1);
+    const int x1 = std::min(g.w - 1, (int)std::floor(g.cx + g.r) + 2);
+    const int y1 = std::min(g.h - 1, (int)std::floor(g.cy + g.r) + 2);
+    Box b;
+    b.x0 = std::min(x0, g.w - 1);
+    b.y0 = std::min(y0, g.h - 1);
+    b.w = std::max(1, x1 - b.x0 + 1);
+    b.h = std::max(1, y1 - b.y0 + 1);
+    b.pitch = (b.w + 3) & ~3;
+    return b;
+}
+
+// device-usable address of a host buffer, or NULL if the device cannot read it
+static const float* device_view(const float* p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer ? static_cast<const float*>(a.devicePointer) : p;
+    int pageable = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+    return pageable ? p : nullptr;
+}
+
+}  // namespace zm
+
+using namespace zm;
+
+extern "C" int zm_upload_disk_bytes(const zm_image_t* host_imgs, int batch, unsigned long long* bytes) {
+    if (!bytes) return set_error(ZM_EINVAL, "bytes is NULL");
+    int s = check_images(host_imgs, batch);
+    if (s != ZM_OK) return s;
+    unsigned long long t = 0;
+    for (int b = 0; b < batch; ++b) {
+        const Box bx = disk_box(host_imgs[b]);
+        t += sizeof(float) * (unsigned long long)bx.pitch * bx.h;
+    }
+    *bytes = t;
+    return ZM_OK;
+}
+
+extern "C" int zm_upload_disk(const zm_image_t* host_imgs, int batch, float* dev, unsigned long long dev_bytes,
+                              zm_image_t* dev_imgs, void* stream) {
+    if (!dev || !dev_imgs) return set_error(ZM_EINVAL, "NULL argument");
+    if ((reinterpret_cast<uintptr_t>(dev) & 15u) != 0) return set_error(ZM_EINVAL, "dev must be 16-byte aligned");
+    int s = check_images(host_imgs, batch);
+    if (s != ZM_OK) return s;
+    int device = 0;
+    ZM_CUDA_TRY(cudaGetDevice(&device));
+    static thread_local UpParams up;
+    up.dev = dev;
+    long long off = 0;
+    for (int c0 = 0; c0 < batch; c0 += UP_MAX_IMG) {
+        const int nc = std::min(UP_MAX_IMG, batch - c0);
+        int max_h = 1;
+        for (int j = 0; j < nc; ++j) {
+            const zm_image_t& im = host_imgs[c0 + j];
+            const float* view = device_view(im.data, device);
+            if (!view)
+                return set_error(ZM_EUNSUPPORTED, "image %d: host memory the device cannot read (pin it or register it)",
+                                 c0 + j);
+            const Box bx = disk_box(im);
+            if ((unsigned long long)(off + (long long)bx.pitch * bx.h) * sizeof(float) > dev_bytes)
+                return set_error(ZM_EINVAL, "dev holds %llu bytes; the boxes need more (zm_upload_disk_bytes)",
+                                 dev_bytes);
+            UpBox& u = up.box[j];
+            u.src = view + (long long)bx.y0 * im.pitch + bx.x0;
+            u.spitch = im.pitch;
+            u.w = bx.w;
+            u.h = bx.h;
+            u.dst = off;
+            u.dpitch = bx.pitch;
+            const GeoImage g = resolve(im);
+            dev_imgs[c0 + j] = zm_image_t{dev + off, bx.h, bx.w, bx.pitch, g.cx - (float)bx.x0, g.cy - (float)bx.y0, g.r};
+            off += (long long)bx.pitch * bx.h;
+            max_h = std::max(max_h, bx.h);
+        }
+        up.n = nc;
+        k_upload_boxes<<<dim3(std::min(max_h, 512), nc), 256, 0, (cudaStream_t)stream>>>(up);
+        ZM_LAUNCH_CHECK("k_upload_boxes");
+    }
+    return ZM_OK;
+}

@@ -77,6 +77,8 @@ SIGNATURES = {
     "zm_moments": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_uint, c_void_p]),
     "zm_moments_ex": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_uint, c_void_p]),
     "zm_moments_polar": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_upload_disk_bytes": (c_int, [c_void_p, c_int, POINTER(ctypes.c_ulonglong)]),
+    "zm_upload_disk": (c_int, [c_void_p, c_int, c_void_p, ctypes.c_ulonglong, c_void_p, c_void_p]),
     "zm_resample": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
     "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
     "zm_project": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
@@ -165,12 +167,27 @@ def image_desc(t, geometry=None):
     return zm_image_t(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), cx, cy, r)
 
 
+def host_image_desc(t, geometry=None):
+    """zm_image_t for a 2-D float32 host image: a CPU tensor (pinned or not) or a
+    numpy array, rows may be strided, unit column stride."""
+    cx, cy, r = _geometry(geometry)
+    if hasattr(t, "data_ptr"):
+        if t.dim() != 2 or str(t.dtype) != "torch.float32" or t.is_cuda or t.stride(1) != 1:
+            raise ValueError("host images must be 2-D float32 CPU tensors with unit column stride")
+        return zm_image_t(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), cx, cy, r)
+    if t.ndim != 2 or t.dtype.name != "float32" or t.strides[1] != 4:
+        raise ValueError("host images must be 2-D float32 arrays with unit column stride")
+    return zm_image_t(t.ctypes.data, t.shape[0], t.shape[1], t.strides[0] // 4, cx, cy, r)
+
+
 def canvas_desc(t, geometry=None):
     d = image_desc(t, geometry)
     return zm_canvas_t(d.data, d.height, d.width, d.pitch, d.cx, d.cy, d.radius)
 
 
 def _images(imgs, geometries=None):
+    if isinstance(imgs, ctypes.Array):                 # descriptors built already (e.g. zm_upload_disk)
+        return imgs, len(imgs)
     imgs = list(imgs)
     geos = list(geometries) if geometries is not None else [None] * len(imgs)
     arr = (zm_image_t * len(imgs))(*[image_desc(t, g) for t, g in zip(imgs, geos)])
@@ -246,6 +263,29 @@ def zm_moments_ex(plan, images, out, fhat=None, flags=0, stream=None, geometries
 
 def zm_moments_polar(plan, fhat, batch, out, flags=0, stream=None):
     _check(lib().zm_moments_polar(plan, _ptr(fhat), batch, _ptr(out), flags, _stream(stream)))
+
+
+def _host_images(imgs, geometries=None):
+    imgs = list(imgs)
+    geos = list(geometries) if geometries is not None else [None] * len(imgs)
+    return (zm_image_t * len(imgs))(*[host_image_desc(t, g) for t, g in zip(imgs, geos)]), len(imgs)
+
+
+def zm_upload_disk_bytes(host_images, geometries=None):
+    arr, n = _host_images(host_images, geometries)
+    b = ctypes.c_ulonglong()
+    _check(lib().zm_upload_disk_bytes(arr, n, ctypes.byref(b)))
+    return b.value
+
+
+def zm_upload_disk(host_images, dev, stream=None, geometries=None):
+    """Copy the disk boxes of host images (pinned tensors / arrays the device can
+    read) into the device tensor `dev`; returns the zm_image_t array of the boxes,
+    to pass as `images` to zm_moments* (reuse it while the buffers stay put)."""
+    arr, n = _host_images(host_images, geometries)
+    out = (zm_image_t * n)()
+    _check(lib().zm_upload_disk(arr, n, _ptr(dev), dev.numel() * dev.element_size(), out, _stream(stream)))
+    return out
 
 
 def zm_resample(plan, images, fhat, stream=None, geometries=None):

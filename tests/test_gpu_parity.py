@@ -424,3 +424,34 @@ def test_4k_bench_configuration_sampled():
         Z = as_complex(out)
         for b, img in ((0, imgs[0]), (B - 1, imgs[1])):
             assert metrics.rel_max_err(Z[b], oracle_moments(img, p)) <= TOL_Z
+
+
+# ------------------------------------------------------------------ host frames -> disk boxes
+@pytest.mark.parametrize("pinned", [True, False])
+def test_upload_disk_boxes_give_the_same_moments(pinned):
+    """zm_upload_disk copies only the disk's bounding box (plus the bilinear
+    margin) of host frames; moments from the boxes match moments from the whole
+    frames on the device (float rounding of the shifted coordinates only)."""
+    frames = [synth.blob_image(270, 480, 6, workload=70, index=b) for b in range(3)]
+    geos = [None, (250.0, 140.0, 100.0), (20.5, 30.0, 60.0)]      # centred, off-centre, clipped by the edge
+    host = [torch.from_numpy(f).pin_memory() if pinned else torch.from_numpy(f) for f in frames]
+    with Plan(40, 64, 128, zm.ZM_PREC_BF16X3) as p:
+        nbytes = zm.zm_upload_disk_bytes(host, geometries=geos)
+        dev_buf = torch.empty(nbytes // 4 + 4, device=DEV)
+        try:
+            boxes = zm.zm_upload_disk(host, dev_buf, geometries=geos)
+        except zm.ZmError as e:                                  # pageable memory on a device that cannot read it
+            assert not pinned and e.status == zm.ZM_EUNSUPPORTED
+            pytest.skip("pageable host memory is not readable by this device")
+        torch.cuda.synchronize()
+        assert sum(b.height * b.width for b in boxes) < 3 * 270 * 480
+        got = torch.empty((3, p.P, 2), device=DEV)
+        zm.zm_moments(p.h, boxes, got)
+        want = gpu_moments(p, frames, geometries=geos)
+        torch.cuda.synchronize()
+        g = as_complex(got)
+    for b in range(3):
+        assert metrics.rel_max_err(g[b], want[b]) <= 1e-5, b
+        ref = om.moments(frames[b].astype(np.float64), 40, 64, 128,
+                         geometry=geos[b] if geos[b] else None)
+        assert metrics.rel_max_err(g[b], ref) <= TOL_Z, b
