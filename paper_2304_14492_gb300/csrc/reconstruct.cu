@@ -156,12 +156,12 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
 #pragma unroll
                 for (int r = 0; r < Q; ++r) {
                     const float2 x = make_float2(0.5f * v[r].x, 0.5f * v[r].y);
-                    if (o) o[lane + L * brev_c<FFT::LOGQ>(r)] = x;
+                    if (o) __stcs(&o[lane + L * brev_c<FFT::LOGQ>(r)], x);   // output, not read again here
                     tbuf[r * 32 + lane] = x;
                 }
                 float2 f[Q];
 #pragma unroll
-                for (int r = 0; r < Q; ++r) f[r] = __ldg(&rf[lane + L * brev_c<FFT::LOGQ>(r)]);
+                for (int r = 0; r < Q; ++r) f[r] = __ldcs(&rf[lane + L * brev_c<FFT::LOGQ>(r)]);   // last use
 #pragma unroll
                 for (int r = 0; r < Q; ++r) {
                     const float2 x = tbuf[r * 32 + lane];
