@@ -52,8 +52,7 @@ def parse_args():
     return ap.parse_args()
 
 
-def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+from paper_2304_14492_gb300.replicas import dist_env, job_throughput, max_over_ranks, shard  # noqa: E402
 
 
 # ---------------------------------------------------------------- clocks
@@ -266,7 +265,7 @@ def run_gb300(args):
         prec = "bf16x3"
     pflag = {"fp32": zm.ZM_PREC_FP32, "bf16x3": zm.ZM_PREC_BF16X3, "fp16x3": zm.ZM_PREC_FP16X3}
     P = zm.zm_num_moments(N_MAX)
-    frames = make_frames(B, start=rank * B)
+    frames = make_frames(B, start=shard(rank, B).start)
     imgs = torch.from_numpy(np.stack(frames)).to(dev)
     views = [imgs[b] for b in range(B)]
     del frames
@@ -329,13 +328,10 @@ def run_gb300(args):
     l1 = zm.zm_launch_count()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     seg = [statistics.mean(e[j].elapsed_time(e[j + 1]) for e in kb) for j in range(3)]
     kb_ms = seg[0]
-    value = world * B * args.steps / (ms / 1000.0)
+    value = job_throughput(world, B, args.steps, ms)
 
     # roofline of the dominant kernel (tile resampler): algorithmic bytes per
     # launch = touched image sectors + polar samples written, per frame
