@@ -335,6 +335,16 @@ int zm_server_reset_stats(zm_server_t server);
 /* Stop the scheduler (after draining at most timeout_s) and free everything. */
 int zm_server_destroy(zm_server_t server, double timeout_s);
 
+/*
+ * Diagnostic (no counterpart in the paper): one kernel waits, through the
+ * bounded mbarrier wait every tensor-core and copy pipeline here uses, on a
+ * barrier whose phase never completes; the wait gives up after its limit
+ * (2 s) and the kernel writes ZM_ETIMEOUT to the device int *status and
+ * returns, leaving the context usable.  Shows that a stalled pipeline ends in
+ * a status, not a hang.  Asynchronous on `stream`.
+ */
+int zm_probe_bounded_wait(int* status, void* stream);
+
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic counter; never reset). */
 unsigned long long zm_launch_count(void);

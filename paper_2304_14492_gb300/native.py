@@ -96,6 +96,7 @@ SIGNATURES = {
     "zm_server_stats": (c_int, [c_void_p, POINTER(zm_server_stats_t)]),
     "zm_server_reset_stats": (c_int, [c_void_p]),
     "zm_server_destroy": (c_int, [c_void_p, c_double]),
+    "zm_probe_bounded_wait": (c_int, [c_void_p, c_void_p]),
     "zm_launch_count": (ctypes.c_ulonglong, []),
     "zm_reconstruct": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_reconstruct_errors": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_uint, c_void_p]),
@@ -286,6 +287,10 @@ def zm_upload_disk(host_images, dev, stream=None, geometries=None):
     out = (zm_image_t * n)()
     _check(lib().zm_upload_disk(arr, n, _ptr(dev), dev.numel() * dev.element_size(), out, _stream(stream)))
     return out
+
+
+def zm_probe_bounded_wait(status, stream=None):
+    _check(lib().zm_probe_bounded_wait(_ptr(status), _stream(stream)))
 
 
 def zm_resample(plan, images, fhat, stream=None, geometries=None):
