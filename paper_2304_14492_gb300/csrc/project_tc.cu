@@ -362,7 +362,8 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
 // MMAs and commits them to the stage's "empty" barrier, and refills the stage
 // of the previous chunk once those MMAs have read it.  The epilogue writes
 // the moments (Neumann factor applied) straight into out[b][idx(n, m)].
-constexpr int BLK_A_BYTES = 16 * 1024;        // A region of a stage: 128 rows x 64 k x 2 B
+constexpr int BLK_A_BYTES = 16 * 1024;        // what the M = 128 MMA reads of an A half: 128 rows x 64 k x 2 B
+constexpr int BLK_CPC_MAX = 4;                // 64-ring chunks per stage, at most
 
 struct BlkParams {
     const uint8_t* Ablk;
@@ -373,7 +374,8 @@ struct BlkParams {
     float* out;
     int* status;
     int n_max, n_chunks, ncol, P;
-    int stages, stage_bytes, b_bytes;   // b_bytes: B region of one half in a stage
+    int stages;              // stage ring
+    int cpc;                 // 64-ring chunks per stage
     int neumann;
     float inv_scale;
 };
@@ -416,61 +418,81 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     const uint32_t sm0 = smem_u32(sm);
 
     if (tid == 0) {
+        // a stage holds p.cpc consecutive 64-ring chunks, each as
+        // [A hi: rg KB][A lo: rg KB][F hi: bg KB][F lo: bg KB]; the M = 128 MMA
+        // reads 16 KB from each A half, past rg KB into whatever follows (a
+        // 16 KB pad after the last stage keeps that inside the allocation):
+        // those rows only feed D rows >= K_m, which are never read
+        const int bg = NT / 8;
+        const uint32_t a_bytes = (uint32_t)rg * 1024u, b_bytes = (uint32_t)bg * 1024u;
+        const uint32_t sub_bytes = 2u * (a_bytes + b_bytes);
+        const int cpc = p.cpc;
+        const uint32_t stage_bytes = cpc * sub_bytes;
         const uint8_t* a_src = p.Ablk + p.ablk_off[m];
         const size_t a_chunk = (size_t)rg * 1024;
         const uint8_t* f_src = p.Fblk + (((size_t)m * nch) * cg + cg0) * 1024;
         const size_t f_chunk = (size_t)cg * 1024;
-        const uint32_t tx = (uint32_t)(2 * (rg + cgt) * 1024);
+        const int nst = (nch + cpc - 1) / cpc;            // stage loads (groups of chunks)
+        auto subs = [&](int c) { return min(cpc, nch - c * cpc); };
         auto load = [&](int c) {
             const int st = c % S;
-            const uint32_t base = sm0 + (uint32_t)st * p.stage_bytes;
+            const uint32_t base = sm0 + (uint32_t)st * stage_bytes;
             const uint32_t bar = smem_u32(&full[st]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
-            bulk_copy(base, a_src + c * a_chunk, (uint32_t)a_chunk, bar);
-            bulk_copy(base + BLK_A_BYTES, a_src + p.ablk_half + c * a_chunk, (uint32_t)a_chunk, bar);
-            bulk_copy(base + 2 * BLK_A_BYTES, f_src + c * f_chunk, (uint32_t)cgt * 1024, bar);
-            bulk_copy(base + 2 * BLK_A_BYTES + p.b_bytes, f_src + p.fblk_half + c * f_chunk, (uint32_t)cgt * 1024,
-                      bar);
+            const int ns = subs(c);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"((uint32_t)ns * 2u * (a_bytes + (uint32_t)cgt * 1024u))
+                         : "memory");
+            for (int j = 0; j < ns; ++j) {
+                const size_t ch = (size_t)c * cpc + j;
+                const uint32_t d = base + j * sub_bytes;
+                bulk_copy(d, a_src + ch * a_chunk, a_bytes, bar);
+                bulk_copy(d + a_bytes, a_src + p.ablk_half + ch * a_chunk, a_bytes, bar);
+                bulk_copy(d + 2 * a_bytes, f_src + ch * f_chunk, (uint32_t)cgt * 1024, bar);
+                bulk_copy(d + 2 * a_bytes + b_bytes, f_src + p.fblk_half + ch * f_chunk, (uint32_t)cgt * 1024, bar);
+            }
         };
         const uint32_t idesc = instr_desc(NT, 0);
         const unsigned long long t0 = global_ns();
         int loaded = 0, done = 0;
         bool ok = true;
-        for (; loaded < nch && loaded < S; ++loaded) load(loaded);
-        for (int c = 0; c < nch && ok; ++c) {
+        for (; loaded < nst && loaded < S; ++loaded) load(loaded);
+        for (int c = 0; c < nst && ok; ++c) {
             const int st = c % S;
             if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c / S) & 1), t0)) {
                 ok = false;
                 break;
             }
-            const uint32_t base = sm0 + (uint32_t)st * p.stage_bytes;
-            const uint32_t ah = base, al = base + BLK_A_BYTES;
-            const uint32_t fh = base + 2 * BLK_A_BYTES, fl = fh + p.b_bytes;
+            const int ns = subs(c);
+            for (int j = 0; j < ns; ++j) {
+                const uint32_t base = sm0 + (uint32_t)st * stage_bytes + j * sub_bytes;
+                const uint32_t ah = base, al = base + a_bytes;
+                const uint32_t fh = base + 2 * a_bytes, fl = fh + b_bytes;
 #pragma unroll
-            for (int ks = 0; ks < TC_KC / 16; ++ks) {
-                const uint32_t off = ks * 256;      // 16 k = two core matrices along K
-                const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
-                const uint64_t dfh = smem_desc(fh + off), dfl = smem_desc(fl + off);
-                const uint32_t acc0 = (c == 0 && ks == 0) ? 0u : 1u;
-                asm volatile(
-                    "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                    "l"(dah), "l"(dfh), "r"(idesc), "r"(acc0));
-                asm volatile(
-                    "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                    "l"(dah), "l"(dfl), "r"(idesc), "r"(1u));
-                asm volatile(
-                    "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                    "l"(dal), "l"(dfh), "r"(idesc), "r"(1u));
+                for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                    const uint32_t off = ks * 256;      // 16 k = two core matrices along K
+                    const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
+                    const uint64_t dfh = smem_desc(fh + off), dfl = smem_desc(fl + off);
+                    const uint32_t acc0 = (c == 0 && j == 0 && ks == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dfh), "r"(idesc), "r"(acc0));
+                    asm volatile(
+                        "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dfl), "r"(idesc), "r"(1u));
+                    asm volatile(
+                        "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                        "l"(dal), "l"(dfh), "r"(idesc), "r"(1u));
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&empty[st]))
                          : "memory");
             done = c + 1;
-            // refill the stage of the previous chunk once its MMAs have read it
-            if (c >= 1 && loaded < nch) {
+            // refill the stage of the previous group once its MMAs have read it
+            if (c >= 1 && loaded < nst) {
                 const int pc = c - 1, ps = pc % S;
                 if (!mbar_wait(smem_u32(&empty[ps]), (uint32_t)((pc / S) & 1), t0)) {
                     ok = false;
@@ -479,7 +501,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
                 load(loaded++);
             }
         }
-        if (ok) ok = mbar_wait(smem_u32(&empty[(nch - 1) % S]), (uint32_t)(((nch - 1) / S) & 1), t0);
+        if (ok) ok = mbar_wait(smem_u32(&empty[(nst - 1) % S]), (uint32_t)(((nst - 1) / S) & 1), t0);
         if (!ok) {
             // a wait ran out: report it, then give the copies and MMAs in flight a
             // bounded time to land before the shared memory and TMEM are released
@@ -595,13 +617,20 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
     bp.n_chunks = p->n_chunks;
     bp.ncol = ncol;
     bp.P = p->P;
-    bp.b_bytes = (nt_max / 8) * 1024;
-    bp.stage_bytes = 2 * BLK_A_BYTES + 2 * bp.b_bytes;
-    const int cap = 200 * 1024;
-    bp.stages = std::max(2, std::min(8, cap / bp.stage_bytes));
+    // chunks per stage: the most (measured: fewer, larger copies pay) that
+    // still leave room for two stages
+    const int rg_max = (p->n_max / 2 + 1 + 7) / 8;
+    const int budget = 225 * 1024 - BLK_A_BYTES;            // the 16 KB pad after the last stage, static smem
+    int cpc = BLK_CPC_MAX;
+    while (cpc > 1 && 2 * cpc * 2 * (rg_max + nt_max / 8) * 1024 > budget) cpc >>= 1;
+    const int stage_max = cpc * 2 * (rg_max + nt_max / 8) * 1024;
+    bp.cpc = cpc;
+    bp.stages = std::min(8, budget / stage_max);
+    if (bp.stages < 2)
+        return set_error(ZM_EUNSUPPORTED, "blocked projection: stages of %d B do not fit", stage_max);
     bp.neumann = (flags & ZM_NEUMANN) ? 1 : 0;
     bp.inv_scale = 1.0f / p->a_scale;
-    const size_t smem = (size_t)bp.stages * bp.stage_bytes;
+    const size_t smem = (size_t)bp.stages * stage_max + BLK_A_BYTES;
     static size_t configured[64] = {0};
     const int dev = p->device;
     if (dev >= 64 || smem > configured[dev]) {
