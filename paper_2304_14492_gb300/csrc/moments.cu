@@ -205,6 +205,165 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
     }
 }
 
+// Polar samples -> ring spectra as bf16 operand blocks (the blocked
+// projection's F), one item = a block of 8 rings of a group of 4 images (one
+// 8-column group of the blocks).  Warp w transforms ring i0 + w of the 4
+// images in turn (the next ring's samples are loaded as soon as the current
+// FFT has left the registers), splits each into F_m, m <= n_max, and stages
+// them as Fs[image][re/im][ring][m]; then 8 consecutive threads write one
+// full 128-byte line (8 columns x 8 rings) per order and half.
+template <int LOGN>
+__global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_blk(const __grid_constant__ KbParams p) {
+    using FFT = RingFFT<LOGN>;
+    constexpr int N = FFT::N;
+    constexpr int ROW = FFT::ROW_FLOATS;
+    constexpr int R = 8;                           // rings per block = warps
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_rho = p.n_rho, n_max = p.n_max, nm1 = n_max + 1;
+    float* rows = smem;                                       // [R][ROW]
+    float* Fs = smem + R * ROW;                               // [4][2][R][nm1]
+    float2* twt = reinterpret_cast<float2*>(smem + ((R * ROW + 64 * nm1 + 3) & ~3));
+    float2* twm = twt + FFT::TW_FLOAT2;                       // e^{-2 pi i m / N}, m <= n_max
+    FFT::load_twiddles(twt, p.tw);
+    for (int m = threadIdx.x; m <= n_max; m += blockDim.x) twm[m] = __ldg(&p.tw[m]);
+    const int n_rb = p.n_chunks * (64 / R);
+    const int g0 = p.b_off >> 2, g1 = (p.b_off + p.nb - 1) >> 2;
+    const int ng = g1 - g0 + 1;
+    const int n_items = n_rb * ng;
+    const int ncol = 2 * p.batch_total;
+    auto in_run = [&](int b) { return b >= p.b_off && b < p.b_off + p.nb; };
+    float2 v[FFT::Q];
+    // the ring of (item, q) for this warp
+    auto load_ring = [&](int item, int q) {
+        const int gi = item / n_rb;
+        const int i = (item - gi * n_rb) * R + warp;
+        const int b = (g0 + gi) * 4 + q;
+        const bool live = lane < FFT::L && i < n_rho && in_run(b);
+        const float* src = p.fhat_in + ((size_t)(live ? b : 0) * n_rho + (live ? i : 0)) * N;
+        if ((reinterpret_cast<uintptr_t>(p.fhat_in) & 7) == 0) {
+            const float2* z = reinterpret_cast<const float2*>(src);
+#pragma unroll
+            for (int s2 = 0; s2 < FFT::Q; ++s2) v[s2] = live ? __ldg(&z[lane + FFT::L * s2]) : make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int s2 = 0; s2 < FFT::Q; ++s2) {
+                const int j = lane + FFT::L * s2;
+                v[s2] = live ? make_float2(__ldg(src + 2 * j), __ldg(src + 2 * j + 1)) : make_float2(0.f, 0.f);
+            }
+        }
+    };
+    if ((int)blockIdx.x < n_items) load_ring(blockIdx.x, 0);
+    __syncthreads();                                          // twiddles
+    float* row = rows + warp * ROW;
+    float2* X = reinterpret_cast<float2*>(row);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int gi = item / n_rb;
+        const int rb = item - gi * n_rb;
+        const int i0 = rb * R;
+        for (int q = 0; q < 4; ++q) {
+            FFT::fwd(v, lane, twt, X);
+            if (lane < FFT::L) {
+#pragma unroll
+                for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::fwd_index(r, lane))] = v[r];
+            }
+            __syncwarp();
+            // the next ring into the registers while this one is split
+            if (q < 3) load_ring(item, q + 1);
+            else if (item + (int)gridDim.x < n_items) load_ring(item + gridDim.x, 0);
+            float* fre = Fs + ((q * 2 + 0) * R + warp) * nm1;
+            float* fim = Fs + ((q * 2 + 1) * R + warp) * nm1;
+            for (int m = lane; m <= n_max; m += 32) {
+                const float2 A = X[FFT::pad(m)];
+                const float2 Bc = cconj(X[FFT::pad((FFT::M - m) & (FFT::M - 1))]);
+                const float2 E = cscale(cadd(A, Bc), 0.5f);
+                const float2 D = csub(A, Bc);
+                const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+                const float2 Fm = cadd(E, cmul(twm[m], O));
+                fre[m] = Fm.x;
+                fim[m] = Fm.y;
+            }
+            __syncwarp();                                     // X is rewritten by the next FFT
+        }
+        __syncthreads();
+        // (m, column) -> one 16-byte row of 8 rings; columns of images outside
+        // this run (or past the batch) are left to their own launch
+        for (int e = threadIdx.x; e < 8 * nm1; e += blockDim.x) {
+            const int col8 = e & 7, m = e >> 3;
+            const int q = col8 >> 1, c = col8 & 1;
+            const int b = (g0 + gi) * 4 + q;
+            if (!in_run(b)) continue;
+            const float* src = Fs + ((q * 2 + c) * R) * nm1 + m;
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float x0 = src[(2 * k) * nm1], x1 = src[(2 * k + 1) * nm1];
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                h[k] = __bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                l[k] = __bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const size_t o = fblk_row(m, i0, 2 * b + c, p.n_chunks, ncol);
+            *reinterpret_cast<uint4*>(p.Fblk + o) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(p.Fblk + p.fblk_half + o) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        __syncthreads();                                      // Fs is refilled for the next item
+    }
+}
+
+template <int LOGN>
+static int launch_blk_t(const KbParams& kp, int nb, cudaStream_t st) {
+    using FFT = RingFFT<LOGN>;
+    const size_t smem = sizeof(float) * (((size_t)8 * FFT::ROW_FLOATS + 64 * (kp.n_max + 1) + 3) & ~(size_t)3) +
+                        sizeof(float2) * ((size_t)FFT::TW_FLOAT2 + kp.n_max + 1);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static size_t configured[64] = {0};
+    if (smem > 48 * 1024 && (dev >= 64 || smem > configured[dev])) {
+        ZM_CUDA_TRY(cudaFuncSetAttribute(k_ring_blk<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev < 64) configured[dev] = smem;
+    }
+    static std::mutex mu;
+    static std::map<size_t, int> resident;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = resident.find(smem);
+        if (it != resident.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ring_blk<LOGN>, 256, smem) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            resident[smem] = per_sm;
+        }
+    }
+    KbParams& k = const_cast<KbParams&>(kp);
+    k.nb = nb;
+    const int ng = ((kp.b_off + nb - 1) >> 2) - (kp.b_off >> 2) + 1;
+    const long long items = (long long)kp.n_chunks * 8 * ng;
+    const int grid = (int)std::min<long long>(items, (long long)per_sm * num_sms(dev));
+    k_ring_blk<LOGN><<<grid, 256, smem, st>>>(kp);
+    ZM_LAUNCH_CHECK("k_ring_blk");
+    return ZM_OK;
+}
+
+static int launch_blk(int logn, const KbParams& kp, int nb, cudaStream_t st) {
+    switch (logn) {
+        case 3: return launch_blk_t<3>(kp, nb, st);
+        case 4: return launch_blk_t<4>(kp, nb, st);
+        case 5: return launch_blk_t<5>(kp, nb, st);
+        case 6: return launch_blk_t<6>(kp, nb, st);
+        case 7: return launch_blk_t<7>(kp, nb, st);
+        case 8: return launch_blk_t<8>(kp, nb, st);
+        case 9: return launch_blk_t<9>(kp, nb, st);
+        case 10: return launch_blk_t<10>(kp, nb, st);
+        case 11: return launch_blk_t<11>(kp, nb, st);
+        default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", logn);
+    }
+}
+
 template <int LOGN, int MODE>
 static int launch_kb_t(const KbParams& kp, int R, int nb, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
@@ -421,7 +580,7 @@ static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int 
     for (int c0 = b0; c0 < b0 + nb; c0 += 65535) {
         const int nc = std::min(65535, b0 + nb - c0);
         kp.b_off = c0;
-        const int s = launch_kb_mode<KB_POLAR>(p->log_theta, kp, R, nc, st);
+        const int s = Fblk ? launch_blk(p->log_theta, kp, nc, st) : launch_kb_mode<KB_POLAR>(p->log_theta, kp, R, nc, st);
         if (s != ZM_OK) return s;
     }
     return ZM_OK;
