@@ -253,6 +253,8 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_blk(const __
             }
         }
     };
+    griddep_wait();                                           // the polar samples are written
+    griddep_launch();
     if ((int)blockIdx.x < n_items) load_ring(blockIdx.x, 0);
     __syncthreads();                                          // twiddles
     float* row = rows + warp * ROW;
@@ -344,8 +346,7 @@ static int launch_blk_t(const KbParams& kp, int nb, cudaStream_t st) {
     const int ng = ((kp.b_off + nb - 1) >> 2) - (kp.b_off >> 2) + 1;
     const long long items = (long long)kp.n_chunks * 8 * ng;
     const int grid = (int)std::min<long long>(items, (long long)per_sm * num_sms(dev));
-    k_ring_blk<LOGN><<<grid, 256, smem, st>>>(kp);
-    ZM_LAUNCH_CHECK("k_ring_blk");
+    ZM_LAUNCH_PDL("k_ring_blk", k_ring_blk<LOGN>, dim3(grid), dim3(256), smem, st, kp);
     return ZM_OK;
 }
 

@@ -414,6 +414,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    griddep_wait();                    // the spectra blocks are written, `out` is free
+    griddep_launch();
     const uint32_t tmem = tslot;
     const uint32_t sm0 = smem_u32(sm);
 
@@ -637,8 +639,7 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
         ZM_CUDA_TRY(cudaFuncSetAttribute(k_project_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (dev < 64) configured[dev] = smem;
     }
-    k_project_blk<<<dim3(p->n_max + 1, tiles), TC_THREADS, smem, st>>>(bp);
-    ZM_LAUNCH_CHECK("k_project_blk");
+    ZM_LAUNCH_PDL("k_project_blk", k_project_blk, dim3(p->n_max + 1, tiles), dim3(TC_THREADS), smem, st, bp);
     return ZM_OK;
 }
 

@@ -129,6 +129,8 @@ __global__ void __launch_bounds__(RT_THREADS) k_recon_tc(const __grid_constant__
             dst += 2 * a + 2 * b;
         }
     }
+    griddep_wait();                    // the moments are written, G is free
+    griddep_launch();
     // the moments of the column tile as Z hi / lo blocks (orders past K_m and
     // columns past the batch are zero)
     {
@@ -304,8 +306,7 @@ int launch_radial_tc(zm_plan_t p, const float* moments, int batch, unsigned flag
     rp.P = p->P;
     rp.ncol = ncol;
     rp.neumann = (flags & ZM_NEUMANN) ? 1 : 0;
-    k_recon_tc<<<dim3(p->n_max + 1, p->n_rtiles, ctiles), RT_THREADS, smem, st>>>(rp);
-    ZM_LAUNCH_CHECK("k_recon_tc");
+    ZM_LAUNCH_PDL("k_recon_tc", k_recon_tc, dim3(p->n_max + 1, p->n_rtiles, ctiles), dim3(RT_THREADS), smem, st, rp);
     return ZM_OK;
 }
 

@@ -112,6 +112,8 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     float2* tbuf = twm + M + warp * FFT::TBUF;                    // per-warp transpose buffer
     FFT::load_twiddles(twt, tw);
     for (int m = threadIdx.x; m < M; m += blockDim.x) twm[m] = __ldg(&tw[m]);
+    griddep_wait();                    // G (and the reference samples) are written, out is free
+    griddep_launch();
     // persistent: the CTA takes ring blocks (b, rb) = item / n_rb, item mod n_rb
     const int n_rb = (n_rho + R - 1) / R;
     for (int item = blockIdx.x; item < n_rb * batch; item += gridDim.x) {
@@ -263,8 +265,8 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
     const long long items = (long long)((n_rho + R - 1) / R) * batch;
     const int slots = sms * resident_blocks(k_recon_ifft<LOGN, ERR>, R * 32, smem);
     const int grid = (int)std::min<long long>(items, slots);
-    k_recon_ifft<LOGN, ERR><<<grid, R * 32, smem, st>>>(G, tw, n_max, n_rho, batch, out, ref, part);
-    ZM_LAUNCH_CHECK("k_recon_ifft");
+    ZM_LAUNCH_PDL("k_recon_ifft", (k_recon_ifft<LOGN, ERR>), dim3(grid), dim3(R * 32), smem, st, G, tw, n_max, n_rho,
+                  batch, out, ref, part);
     return ZM_OK;
 }
 
@@ -344,8 +346,8 @@ int launch_reconstruct_errors(zm_plan_t p, const float* moments, int batch, floa
     double* part = (double*)p->ws_red.ptr;
     s = launch_ifft<true>(p, G, batch, out, fhat, part, st);
     if (s != ZM_OK) return s;
-    k_reduce_records<<<(batch + 3) / 4, 128, 0, st>>>(part, nrec, batch, err);
-    ZM_LAUNCH_CHECK("k_reduce_records");
+    ZM_LAUNCH_PDL("k_reduce_records", k_reduce_records, dim3((batch + 3) / 4), dim3(128), 0, st, (const double*)part,
+                  nrec, batch, err);
     return ZM_OK;
 }
 
@@ -571,6 +573,8 @@ __global__ void k_reduce_final(const double* __restrict__ part, int batch, int m
 // out[b] = (eps_1, eps, f_max, count) from nrec records (sd, sf, max, count)
 // per image; one warp per image.
 __global__ void k_reduce_records(const double* __restrict__ part, int nrec, int batch, double* __restrict__ out) {
+    griddep_wait();                    // the records are written
+    griddep_launch();
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= batch) return;

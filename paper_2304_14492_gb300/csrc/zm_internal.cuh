@@ -29,6 +29,39 @@ int cuda_error(cudaError_t e, const char* what);
         ::zm::count_launch();                                    \
     } while (0)
 
+// Programmatic dependent launch: a kernel launched this way may start while
+// the previous kernel of the stream is finishing.  It runs its prologue (shared
+// memory, TMEM, barriers, reads of plan constants) and then griddep_wait(),
+// which returns once the previous kernel has completed and its writes are
+// visible; nothing before that wait may read or write memory the previous
+// kernels use.  griddep_launch() lets the next kernel start early.  Both are
+// no-ops when the launch carries no programmatic dependency.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+#define ZM_LAUNCH_PDL(what, kernel, grid, block, smem, st, ...)                         \
+    do {                                                                              \
+        cudaError_t _e = ::zm::launch_pdl(kernel, grid, block, smem, st, __VA_ARGS__);  \
+        if (_e != cudaSuccess) return ::zm::cuda_error(_e, what);                     \
+        ::zm::count_launch();                                                         \
+    } while (0)
+
 // Makes `dev` current for the lifetime of the guard and restores the caller's
 // device afterwards.
 struct DeviceGuard {
