@@ -1,5 +1,5 @@
 // Radial part of the reconstruction (Eq. 9) on the tensor cores:
-//   G[b][m][re/im][i] = c_m sum_{n = m, m+2, ..} R_nm(rho_i) Z_nm,
+//   G(b, i, m, re/im) = c_m sum_{n = m, m+2, ..} R_nm(rho_i) Z_nm (layout g_index),
 // per m the contraction (rings i) x (orders n) x (image columns), i.e. an MMA
 // with the rings on M (128 per CTA), the columns 2b + re/im on N and the K_m
 // orders on K.  R is split into bf16 hi + lo once per plan and kept as
@@ -71,7 +71,7 @@ struct RtParams {
     const long long* rblk_off;
     long long rblk_half;
     const float* Z;          // [batch][P][2]
-    float* G;                // [batch][n_max+1][2][n_rho]
+    float* G;                // layout g_index
     int* status;
     int n_max, n_rho, P, ncol;
     int neumann;
@@ -238,8 +238,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_recon_tc(const __grid_constant__
                 for (int j = 0; j < 16; ++j) {
                     const int gcol = ct * RT_NMAX + c0 + j;
                     if (c0 + j < cols_t)
-                        p.G[(((size_t)(gcol >> 1) * nm1 + m) * 2 + (gcol & 1)) * p.n_rho + i] =
-                            cm * __uint_as_float(r[j]);
+                        p.G[g_index(gcol >> 1, i, m, gcol & 1, (p.n_rho + 7) / 8, nm1)] = cm * __uint_as_float(r[j]);
                 }
             }
         }

@@ -15,7 +15,7 @@ constexpr int KD_MAX_IMG = 128;
 constexpr float kTwoPi = 6.28318530717958647692f;
 
 // ============================================================== radial part
-// G[b][m][re/im][i] = c_m sum_{n = m, m+2, ..} R_nm(rho_i) Z_nm, with
+// G(b, i, m, re/im) = c_m sum_{n = m, m+2, ..} R_nm(rho_i) Z_nm (layout g_index), with
 // c_m = 2/eps_m (c_0 = 1, c_m = 2) for the literal Eq. 9 and c_m = 1 for the
 // half sum over the stored m >= 0.  One thread = one node i, one m and RB
 // images (their moments staged in shared memory), so each table value is
@@ -71,9 +71,9 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 #pragma unroll
     for (int bb = 0; bb < RB; ++bb) {
         if (bb < nb) {
-            float* g = G + (((size_t)(b0 + bb) * (n_max + 1) + m) * 2) * n_rho + i;
-            g[0] = c * re[bb];
-            g[n_rho] = c * im[bb];
+            const int nrb = (n_rho + 7) / 8;
+            G[g_index(b0 + bb, i, m, 0, nrb, n_max + 1)] = c * re[bb];
+            G[g_index(b0 + bb, i, m, 1, nrb, n_max + 1)] = c * im[bb];
         }
     }
 }
@@ -119,15 +119,16 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     for (int item = blockIdx.x; item < n_rb * batch; item += gridDim.x) {
         const int b = item / n_rb, rb = item - b * n_rb;
         const int i0 = rb * R;
-        for (int e = threadIdx.x; e < nm1 * R; e += blockDim.x) {
-            const int r = e % R, m = e / R;
-            const int i = i0 + r;
-            float2 g = make_float2(0.f, 0.f);
-            if (i < n_rho) {
-                const float* gp = G + (((size_t)b * nm1 + m) * 2) * n_rho + i;
-                g = make_float2(__ldg(gp), __ldg(gp + n_rho));
-            }
-            Gs[r * nm1 + m] = g;
+        // this block's G is one contiguous run of nm1 x 16 floats (g_index)
+        const float4* gb = reinterpret_cast<const float4*>(G + g_index(b, i0, 0, 0, n_rb, nm1));
+        float* gsf = reinterpret_cast<float*>(Gs);
+        for (int e = threadIdx.x; e < nm1 * 4; e += blockDim.x) {
+            const float4 q4 = __ldg(&gb[e]);
+            const int m = e >> 2, c = (e >> 1) & 1, r0 = (e & 1) * 4;
+            gsf[2 * ((r0 + 0) * nm1 + m) + c] = q4.x;
+            gsf[2 * ((r0 + 1) * nm1 + m) + c] = q4.y;
+            gsf[2 * ((r0 + 2) * nm1 + m) + c] = q4.z;
+            gsf[2 * ((r0 + 3) * nm1 + m) + c] = q4.w;
         }
         __syncthreads();
         const float2* Gr = Gs + warp * nm1;
@@ -296,7 +297,7 @@ static int launch_ifft(zm_plan_t p, const float* G, int batch, float* out, const
 
 static int launch_radial(zm_plan_t p, const float* moments, int batch, unsigned flags, cudaStream_t st,
                          float** G_out) {
-    const int s = p->ws_G.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
+    const int s = p->ws_G.grow(sizeof(float) * g_floats(batch, p->n_rho, p->n_max));
     if (s != ZM_OK) return s;
     float* G = (float*)p->ws_G.ptr;
     if (p->Rblk) {
@@ -318,7 +319,7 @@ static int launch_radial(zm_plan_t p, const float* moments, int batch, unsigned 
         dim3 grid((p->n_rho + 127) / 128, p->n_max + 1, nzc);
         k_recon_radial<<<grid, 128, smem, st>>>(p->R32m, (const float2*)moments + (size_t)b0 * p->P, p->mrow,
                                                  p->n_max, p->n_rho, p->P, nbc, (flags & ZM_NEUMANN) ? 1 : 0,
-                                                 G + (size_t)b0 * (p->n_max + 1) * 2 * p->n_rho);
+                                                 G + g_floats(b0, p->n_rho, p->n_max));
         ZM_LAUNCH_CHECK("k_recon_radial");
     }
     *G_out = G;

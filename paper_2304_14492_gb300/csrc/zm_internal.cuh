@@ -191,6 +191,17 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
 int build_recon_blocks(zm_plan_t p);
 int launch_radial_tc(zm_plan_t p, const float* moments, int batch, unsigned flags, float* G, cudaStream_t st);
 
+// Radial reconstruction spectra G (Eq. 9), ring-block-major so that the 8 rings
+// an inverse-FFT block transforms are one contiguous run: image b, ring i,
+// order m, re/im c at ((b * nrb + i / 8) * (n_max + 1) + m) * 16 + c * 8 + i % 8,
+// nrb = ceil(n_rho / 8).
+__host__ __device__ inline size_t g_index(int b, int i, int m, int c, int nrb, int nm1) {
+    return ((((size_t)b * nrb + (i >> 3)) * nm1 + m) << 4) + (c << 3) + (i & 7);
+}
+__host__ __device__ inline size_t g_floats(int batch, int n_rho, int n_max) {
+    return (size_t)batch * ((n_rho + 7) / 8) * (n_max + 1) * 16;
+}
+
 // Layout of the spectra blocks: half-size in bytes, and the byte offset of the
 // 16-byte row holding F[m][col][i .. i+7] (i a multiple of 8) within a half.
 __host__ __device__ inline size_t fblk_half_bytes(int n_max, int n_chunks, int ncol) {
