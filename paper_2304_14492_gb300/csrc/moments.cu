@@ -722,8 +722,8 @@ extern "C" int zm_plan_reserve(zm_plan_t plan, int batch) {
     if (s == ZM_OK) s = plan->ws_part.grow(sizeof(float) * S * plan->P * 2 * nb);
     if (s == ZM_OK) s = plan->ws_colmax.grow(sizeof(unsigned) * 2 * nb);
     if (s == ZM_OK) s = plan->ws_G.grow(sizeof(float) * g_floats(batch, plan->n_rho, plan->n_max));
-    // reductions: 64 records per image (pixel errors) or one per 8 rings (fused errors)
-    const size_t rec = std::max<size_t>(64, (size_t)(plan->n_rho + 7) / 8);
+    // reductions: 64 records per image (pixel errors) or one per ring (fused errors)
+    const size_t rec = std::max<size_t>(64, (size_t)plan->n_rho);
     if (s == ZM_OK) s = plan->ws_red.grow(sizeof(double) * nb * rec * 4);
     if (s == ZM_OK) s = plan->ws_scale.grow(sizeof(float) * 2 * nb);
     if (s == ZM_OK && blocked_projection(plan))

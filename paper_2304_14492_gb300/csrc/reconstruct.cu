@@ -89,10 +89,10 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // across lanes, so f~ is written (and the reference read) with coalesced
 // accesses from registers.  The grid is persistent: each CTA loads the
 // twiddles once and walks blocks of R rings (b, rb).
-// With ERR, the CTA also accumulates, against the reference polar samples
-// `ref`, sum (ref - f~)^2, sum ref^2, max ref and the node count over the rings
-// of a block into one record part[b][rb] (Eq. 10 / Eq. 13 on the polar nodes);
-// `out` may then be NULL.
+// With ERR, each warp also accumulates, against the reference polar samples
+// `ref`, sum (ref - f~)^2, sum ref^2, max ref and the node count of its ring
+// into one record part[b][i] (Eq. 10 / Eq. 13 on the polar nodes); `out` may
+// then be NULL.
 template <int LOGN, bool ERR>
 __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4))
 k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho, int batch,
@@ -103,7 +103,6 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     constexpr int L = FFT::L;
     constexpr int Q = FFT::Q;
     extern __shared__ __align__(16) float2 Gs[];              // [R][n_max+1]
-    __shared__ float red[8][4];
     const int R = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nm1 = n_max + 1;
@@ -207,30 +206,15 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
                 cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
             }
-            if (lane == 0) {
-                red[warp][0] = sd;
-                red[warp][1] = sf;
-                red[warp][2] = mx;
-                red[warp][3] = cnt;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double a = 0, c = 0, n = 0;
-                float m = -INFINITY;
-                for (int w = 0; w < R; ++w) {
-                    a += red[w][0];
-                    c += red[w][1];
-                    m = fmaxf(m, red[w][2]);
-                    n += red[w][3];
-                }
-                double* o = part + ((size_t)b * n_rb + rb) * 4;
-                o[0] = a;
-                o[1] = c;
-                o[2] = (double)m;
-                o[3] = n;
+            if (lane == 0 && i < n_rho) {
+                double* o = part + ((size_t)b * n_rho + i) * 4;
+                o[0] = sd;
+                o[1] = sf;
+                o[2] = (double)mx;
+                o[3] = cnt;
             }
         }
-        __syncthreads();   // Gs and red are refilled for the next ring block
+        __syncthreads();   // Gs is refilled for the next ring block
     }
 }
 
@@ -341,14 +325,14 @@ int launch_reconstruct_errors(zm_plan_t p, const float* moments, int batch, floa
     float* G = nullptr;
     int s = launch_radial(p, moments, batch, flags, st, &G);
     if (s != ZM_OK) return s;
-    const int nrec = (p->n_rho + 7) / 8;
+    const int nrec = p->n_rho;                 // one record per ring
     s = p->ws_red.grow(sizeof(double) * (size_t)batch * nrec * 4);
     if (s != ZM_OK) return s;
     double* part = (double*)p->ws_red.ptr;
     s = launch_ifft<true>(p, G, batch, out, fhat, part, st);
     if (s != ZM_OK) return s;
-    ZM_LAUNCH_PDL("k_reduce_records", k_reduce_records, dim3((batch + 3) / 4), dim3(128), 0, st, (const double*)part,
-                  nrec, batch, err);
+    ZM_LAUNCH_PDL("k_reduce_records", k_reduce_records, dim3(batch), dim3(256), 0, st, (const double*)part, nrec,
+                  batch, err);
     return ZM_OK;
 }
 
@@ -572,20 +556,23 @@ __global__ void k_reduce_final(const double* __restrict__ part, int batch, int m
 }
 
 // out[b] = (eps_1, eps, f_max, count) from nrec records (sd, sf, max, count)
-// per image; one warp per image.
+// per image.
 __global__ void k_reduce_records(const double* __restrict__ part, int nrec, int batch, double* __restrict__ out) {
     griddep_wait();                    // the records are written
     griddep_launch();
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= batch) return;
+    // one block per image; records summed in a fixed order (thread stride,
+    // then the warp tree, then the warps in order): deterministic
+    __shared__ double red[8][4];
+    const int b = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double sd = 0, sf = 0, cnt = 0, mx = -INFINITY;
-    for (int j = lane; j < nrec; j += 32) {
-        const double* o = part + ((size_t)b * nrec + j) * 4;
-        sd += o[0];
-        sf += o[1];
-        mx = fmax(mx, o[2]);
-        cnt += o[3];
+    const double2* rec = reinterpret_cast<const double2*>(part + (size_t)b * nrec * 4);
+    for (int j = threadIdx.x; j < nrec; j += blockDim.x) {
+        const double2 a = __ldg(&rec[2 * j]), c = __ldg(&rec[2 * j + 1]);
+        sd += a.x;
+        sf += a.y;
+        mx = fmax(mx, c.x);
+        cnt += c.y;
     }
     for (int o = 16; o; o >>= 1) {
         sd += __shfl_xor_sync(0xffffffffu, sd, o);
@@ -593,7 +580,22 @@ __global__ void k_reduce_records(const double* __restrict__ part, int nrec, int 
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
-    if (lane) return;
+    if (lane == 0) {
+        red[warp][0] = sd;
+        red[warp][1] = sf;
+        red[warp][2] = mx;
+        red[warp][3] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    sd = sf = cnt = 0;
+    mx = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sd += red[w][0];
+        sf += red[w][1];
+        mx = fmax(mx, red[w][2]);
+        cnt += red[w][3];
+    }
     out[4 * b + 0] = sd / sf;
     out[4 * b + 1] = sd / (mx * mx * cnt);
     out[4 * b + 2] = mx;
