@@ -14,15 +14,6 @@ namespace zm {
 
 int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, cudaStream_t st);
 
-static int num_sms(int dev) {
-    static int cached[64] = {0};
-    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-    if (dev >= 0 && dev < 64) cached[dev] = n;
-    return n;
-}
-
 // ============================================================== K-b
 constexpr int KB_MAX_IMG = 128;
 

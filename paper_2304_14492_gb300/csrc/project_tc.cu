@@ -278,12 +278,6 @@ __global__ void k_project_reduce_tc(const float* __restrict__ part, int S, int P
     out[(size_t)idx * 2 + 1] = im * f;
 }
 
-static int num_sms_tc(int dev) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-    return n;
-}
-
 int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, cudaStream_t st) {
     if (!p->Ahi || !p->Alo) return set_error(ZM_EINVAL, "plan has no tensor-core operands");
     const int ncol = 2 * batch;
@@ -301,7 +295,7 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
     const int base = (p->n_max + 1) * ctiles;
     // enough CTAs to cover the load -> MMA latency: up to one 64-wide chunk of
     // the radial index per CTA, at most 32 slices
-    const int target = (p->tune_split > 0 ? p->tune_split : 8) * num_sms_tc(p->device);
+    const int target = (p->tune_split > 0 ? p->tune_split : 8) * num_sms(p->device);
     const int kchunks = (p->n_rho + TC_KC - 1) / TC_KC;
     int S = std::max(1, std::min(std::min(kchunks, 32), (target + base - 1) / base));
     const int chunk = ((kchunks + S - 1) / S) * TC_KC;
@@ -362,6 +356,11 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
 // MMAs and commits them to the stage's "empty" barrier, and refills the stage
 // of the previous chunk once those MMAs have read it.  The epilogue writes
 // the moments (Neumann factor applied) straight into out[b][idx(n, m)].
+// With ksplit = 2 the radial range is split between the two CTAs of a
+// cluster (blockIdx.z = 0, 1): rank 1 stores its partial D into a buffer in
+// rank 0's shared memory, and rank 0 adds it to its own after a cluster
+// barrier, in a fixed order (deterministic).  Halving the chunks per CTA
+// halves the longest copy stream and spreads the orders over twice the SMs.
 constexpr int BLK_A_BYTES = 16 * 1024;        // what the M = 128 MMA reads of an A half: 128 rows x 64 k x 2 B
 constexpr int BLK_CPC_MAX = 4;                // 64-ring chunks per stage, at most
 
@@ -376,9 +375,21 @@ struct BlkParams {
     int n_max, n_chunks, ncol, P;
     int stages;              // stage ring
     int cpc;                 // 64-ring chunks per stage
+    int ksplit;              // 1, or 2: the radial range split over a cluster of two CTAs
+    int buf_off;             // byte offset of rank 0's receive buffer (ksplit = 2)
     int neumann;
     float inv_scale;
 };
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
 
 __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constant__ BlkParams p) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -386,7 +397,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     __shared__ __align__(8) uint64_t empty[8];
     __shared__ uint32_t tslot;
     __shared__ int okflag;
-    const int m = blockIdx.x, t = blockIdx.y;
+    const int m = blockIdx.x, t = blockIdx.y, z = blockIdx.z;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Km = (p.n_max - m) / 2 + 1;
     const int rg = (Km + 7) / 8;
@@ -396,7 +407,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     const int NT = ((cols_t + 15) / 16) * 16;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)NT) ncols <<= 1;
-    const int S = p.stages, nch = p.n_chunks;
+    // this CTA's chunks of the radial range
+    const int per = (p.n_chunks + p.ksplit - 1) / p.ksplit;
+    const int c_begin = z * per;
+    const int S = p.stages, nch = min(per, p.n_chunks - c_begin);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
@@ -414,6 +428,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (p.ksplit > 1) cluster_sync_all();     // both CTAs of the pair run before any shared memory crosses
     griddep_wait();                    // the spectra blocks are written, `out` is free
     griddep_launch();
     const uint32_t tmem = tslot;
@@ -430,10 +445,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
         const uint32_t sub_bytes = 2u * (a_bytes + b_bytes);
         const int cpc = p.cpc;
         const uint32_t stage_bytes = cpc * sub_bytes;
-        const uint8_t* a_src = p.Ablk + p.ablk_off[m];
         const size_t a_chunk = (size_t)rg * 1024;
-        const uint8_t* f_src = p.Fblk + (((size_t)m * nch) * cg + cg0) * 1024;
+        const uint8_t* a_src = p.Ablk + p.ablk_off[m] + (size_t)c_begin * a_chunk;
         const size_t f_chunk = (size_t)cg * 1024;
+        const uint8_t* f_src = p.Fblk + (((size_t)m * p.n_chunks + c_begin) * cg + cg0) * 1024;
         const int nst = (nch + cpc - 1) / cpc;            // stage loads (groups of chunks)
         auto subs = [&](int c) { return min(cpc, nch - c * cpc); };
         auto load = [&](int c) {
@@ -519,26 +534,66 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     // epilogue: TMEM lane = row n_local of D (warp w owns lanes 32w..32w+31)
-    if (okflag && warp * 32 < Km) {
-        const int nl = warp * 32 + lane;
+    auto tmem_ld16 = [&](int c0, uint32_t (&r)[16]) {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    };
+    const int nl = warp * 32 + lane;
+    const int bstride = NT + 4;                       // floats per buffer row (16-byte rows, conflict-free)
+    const uint32_t buf = sm0 + (uint32_t)p.buf_off;   // rank 0's receive buffer [row][bstride]
+    if (p.ksplit > 1) {
+        // tcgen05.ld is warp-wide: the condition is uniform per warp, the
+        // stores are per row
+        if (z == 1 && okflag && warp * 32 < Km) {
+            // the partial D rows go to the same place in rank 0's shared memory
+            const uint32_t dst = cluster_map(buf + (uint32_t)(nl * bstride) * 4u, 0);
+            for (int c0 = 0; c0 < NT; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(c0, r);
+                if (nl < Km) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                         dst + (uint32_t)(c0 + j) * 4u),
+                                     "r"(r[j]), "r"(r[j + 1]), "r"(r[j + 2]), "r"(r[j + 3])
+                                     : "memory");
+                }
+            }
+        }
+        __syncwarp();
+        cluster_sync_all();                           // rank 1's rows are in rank 0's buffer
+    }
+    if (okflag && z == 0 && warp * 32 < Km) {
         const bool live = nl < Km;
         const int idx = live ? moment_index(m + 2 * nl, m) : 0;
         const float f = p.inv_scale * ((p.neumann && m == 0) ? 0.5f : 1.f);
+        const float* bufp = reinterpret_cast<const float*>(sm + p.buf_off) + nl * bstride;
         for (int c0 = 0; c0 < NT; c0 += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_ld16(c0, r);
             if (live) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+                if (p.ksplit > 1) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        const float4 q = *reinterpret_cast<const float4*>(bufp + c0 + j);
+                        v[j] += q.x;
+                        v[j + 1] += q.y;
+                        v[j + 2] += q.z;
+                        v[j + 3] += q.w;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = t * 256 + c0 + j;
-                    if (c0 + j < cols_t) p.out[((size_t)(col >> 1) * p.P + idx) * 2 + (col & 1)] = __uint_as_float(r[j]) * f;
+                    if (c0 + j < cols_t) p.out[((size_t)(col >> 1) * p.P + idx) * 2 + (col & 1)] = v[j] * f;
                 }
             }
         }
@@ -620,24 +675,48 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
     bp.ncol = ncol;
     bp.P = p->P;
     // chunks per stage: the most (measured: fewer, larger copies pay) that
-    // still leave room for two stages
+    // still leave room for two stages within `cap` bytes after `tail`
     const int rg_max = (p->n_max / 2 + 1 + 7) / 8;
-    const int budget = 225 * 1024 - BLK_A_BYTES;            // the 16 KB pad after the last stage, static smem
-    int cpc = BLK_CPC_MAX;
-    while (cpc > 1 && 2 * cpc * 2 * (rg_max + nt_max / 8) * 1024 > budget) cpc >>= 1;
-    const int stage_max = cpc * 2 * (rg_max + nt_max / 8) * 1024;
+    auto stage_bytes = [&](int c) { return c * 2 * (rg_max + nt_max / 8) * 1024; };
+    auto fit = [&](int cap, int tail, int* cpc, int* stages) {
+        const int budget = cap - tail;
+        int c = BLK_CPC_MAX;
+        while (c > 1 && 2 * stage_bytes(c) > budget) c >>= 1;
+        *cpc = c;
+        *stages = std::min(8, budget / stage_bytes(c));
+        return *stages >= 2;
+    };
+    // split the radial range over a cluster of two CTAs when every order's
+    // pair fits on the SMs in one wave at two CTAs per SM; rank 0's receive
+    // buffer (rows of nt_max + 4 floats) doubles as the pad after the stages
+    const int rows = ((p->n_max / 2 + 1 + 31) / 32) * 32;
+    const int buf_bytes = rows * (nt_max + 4) * 4;
+    const int tail2 = std::max(BLK_A_BYTES, buf_bytes);
+    const int cap2 = 114 * 1024;                                 // half an SM's shared memory, less reserves
+    int cpc = 0, stages = 0;
+    bool split = p->n_chunks >= 2 && 2 * (p->n_max + 1) * tiles <= 2 * num_sms(p->device) &&
+                 fit(cap2, tail2, &cpc, &stages);
+    if (!split && !fit(225 * 1024, BLK_A_BYTES, &cpc, &stages))
+        return set_error(ZM_EUNSUPPORTED, "blocked projection: stages of %d B do not fit", stage_bytes(1));
     bp.cpc = cpc;
-    bp.stages = std::min(8, budget / stage_max);
-    if (bp.stages < 2)
-        return set_error(ZM_EUNSUPPORTED, "blocked projection: stages of %d B do not fit", stage_max);
+    bp.stages = stages;
+    bp.ksplit = split ? 2 : 1;
+    bp.buf_off = stages * stage_bytes(cpc);
     bp.neumann = (flags & ZM_NEUMANN) ? 1 : 0;
     bp.inv_scale = 1.0f / p->a_scale;
-    const size_t smem = (size_t)bp.stages * stage_max + BLK_A_BYTES;
+    const size_t smem = (size_t)bp.buf_off + (split ? tail2 : BLK_A_BYTES);
     static size_t configured[64] = {0};
     const int dev = p->device;
     if (dev >= 64 || smem > configured[dev]) {
         ZM_CUDA_TRY(cudaFuncSetAttribute(k_project_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (dev < 64) configured[dev] = smem;
+    }
+    if (split) {
+        cudaError_t e = launch_pdl_cluster(k_project_blk, dim3(p->n_max + 1, tiles, 2), dim3(TC_THREADS),
+                                           dim3(1, 1, 2), smem, st, bp);
+        if (e != cudaSuccess) return cuda_error(e, "k_project_blk");
+        count_launch();
+        return ZM_OK;
     }
     ZM_LAUNCH_PDL("k_project_blk", k_project_blk, dim3(p->n_max + 1, tiles), dim3(TC_THREADS), smem, st, bp);
     return ZM_OK;
