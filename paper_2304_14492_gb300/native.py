@@ -186,6 +186,12 @@ def canvas_desc(t, geometry=None):
     return zm_canvas_t(d.data, d.height, d.width, d.pitch, d.cx, d.cy, d.radius)
 
 
+def image_array(images, geometries=None):
+    """The zm_image_t array of a list of 2-D float32 CUDA tensors, to be built
+    once and passed to the image entry points in place of the list."""
+    return _images(images, geometries)[0]
+
+
 def _images(imgs, geometries=None):
     if isinstance(imgs, ctypes.Array):                 # descriptors built already (e.g. zm_upload_disk)
         return imgs, len(imgs)
