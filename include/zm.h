@@ -162,20 +162,28 @@ int zm_moments_polar(zm_plan_t plan, const float* fhat, int batch, float* out,
 /*
  * Host frames -> device disk boxes (no counterpart in the paper; the data
  * movement in front of Eq. 1).  Only the pixels a polar sample's bilinear
- * stencil can touch are needed: for each image, the bounding box of its disk,
- * columns floor(cx - r) - 1 (rounded down to a multiple of 4) .. floor(cx + r)
- * + 2 and rows floor(cy - r) - 1 .. floor(cy + r) + 2, clipped to the image.  A kernel copies each box from `host_imgs[b].data` (host memory
- * the device can read: pinned or registered, or pageable where the device
- * reaches pageable memory through the host page tables) into `dev`, boxes
- * packed one after another with a 16-byte multiple as pitch, and fills
- * `dev_imgs[b]` with the device descriptor of the box and the shifted
- * geometry (explicit cx, cy, radius), so that zm_moments* on dev_imgs gives
- * the moments of the host images.  `dev` (device, 16-byte aligned) must hold
- * zm_upload_disk_bytes(...) bytes.  Asynchronous on `stream`: the host images
- * must stay valid until it has run.  ZM_EUNSUPPORTED if a host buffer cannot
- * be read by the device; ZM_EINVAL for bad sizes or a short `dev`.
+ * stencil can touch are needed.  For each image the device buffer holds the
+ * bounding box of its disk, columns floor(cx - r) - 1 (rounded down to a
+ * multiple of 4) .. floor(cx + r) + 2 and rows floor(cy - r) - 1 ..
+ * floor(cy + r) + 2, clipped to the image, boxes packed one after another with
+ * a 16-byte multiple as pitch.  Of box row y only the span the disk covers is
+ * copied: columns floor(cx - hw) - 3 (rounded down to a multiple of 4) ..
+ * floor(cx + hw) + 3 with hw = sqrt(r^2 - d^2), d = max(0, |y - cy| - 1),
+ * clipped to the box (rows with d >= r: none); the other pixels of the box
+ * are left as they were, and no entry point reads them.  A kernel copies the
+ * spans from `host_imgs[b].data` (host memory the device can read: pinned or
+ * registered, or pageable where the device reaches pageable memory through
+ * the host page tables) into `dev` and fills `dev_imgs[b]` with the device
+ * descriptor of the box and the shifted geometry (explicit cx, cy, radius), so
+ * that zm_moments* on dev_imgs gives the moments of the host images.  `dev`
+ * (device, 16-byte aligned) must hold zm_upload_disk_bytes(...) bytes;
+ * zm_upload_disk_traffic(...) gives the bytes a call reads from the host.
+ * Asynchronous on `stream`: the host images must stay valid until it has run.
+ * ZM_EUNSUPPORTED if a host buffer cannot be read by the device; ZM_EINVAL for
+ * bad sizes or a short `dev`.
  */
 int zm_upload_disk_bytes(const zm_image_t* host_imgs, int batch, unsigned long long* bytes);
+int zm_upload_disk_traffic(const zm_image_t* host_imgs, int batch, unsigned long long* bytes);
 int zm_upload_disk(const zm_image_t* host_imgs, int batch, float* dev, unsigned long long dev_bytes,
                    zm_image_t* dev_imgs, void* stream);
 

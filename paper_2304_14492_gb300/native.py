@@ -78,6 +78,7 @@ SIGNATURES = {
     "zm_moments_ex": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_uint, c_void_p]),
     "zm_moments_polar": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_upload_disk_bytes": (c_int, [c_void_p, c_int, POINTER(ctypes.c_ulonglong)]),
+    "zm_upload_disk_traffic": (c_int, [c_void_p, c_int, POINTER(ctypes.c_ulonglong)]),
     "zm_upload_disk": (c_int, [c_void_p, c_int, c_void_p, ctypes.c_ulonglong, c_void_p, c_void_p]),
     "zm_resample": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
     "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
@@ -282,6 +283,14 @@ def zm_upload_disk_bytes(host_images, geometries=None):
     arr, n = _host_images(host_images, geometries)
     b = ctypes.c_ulonglong()
     _check(lib().zm_upload_disk_bytes(arr, n, ctypes.byref(b)))
+    return b.value
+
+
+def zm_upload_disk_traffic(host_images, geometries=None):
+    """Bytes zm_upload_disk reads from the host for these images."""
+    arr, n = _host_images(host_images, geometries)
+    b = ctypes.c_ulonglong()
+    _check(lib().zm_upload_disk_traffic(arr, n, ctypes.byref(b)))
     return b.value
 
 

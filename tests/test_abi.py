@@ -71,3 +71,32 @@ def test_no_gpu_plan_fails_cleanly(zm):
     with pytest.raises(zm.ZmError) as e:
         zm.zm_plan(4, 8, 16)
     assert e.value.status == zm.ZM_ECUDA
+
+
+def test_upload_traffic_lies_between_the_stencils_and_the_box(zm):
+    """zm_upload_disk_traffic (host logic, no GPU): at least the bytes of the
+    columns the bilinear stencils of the oracle's polar samples touch in each
+    row (from the 4-aligned first column), at most that plus the spans' margins,
+    and less than the bounding box."""
+    import numpy as np
+    from oracle import grid
+    h, w, n_rho, n_theta = 270, 480, 135, 512
+    img = np.zeros((h, w), np.float32)
+    host = [img]
+    traffic = zm.zm_upload_disk_traffic(host)
+    box = zm.zm_upload_disk_bytes(host)
+    rho, _ = grid.radial_nodes(n_rho)
+    theta = 2 * np.pi * np.arange(n_theta) / n_theta
+    X, Y = grid.polar_to_pixel(rho[:, None], theta[None, :], grid.default_geometry(h, w))
+    x0, y0 = np.floor(X).astype(int).ravel(), np.floor(Y).astype(int).ravel()
+    lo, hi = {}, {}
+    for dy in (0, 1):
+        for dx in (0, 1):
+            xs, ys = x0 + dx, y0 + dy
+            ok = (xs >= 0) & (xs < w) & (ys >= 0) & (ys < h)
+            for x, y in zip(xs[ok], ys[ok]):
+                lo[y] = min(lo.get(y, x), x)
+                hi[y] = max(hi.get(y, x), x)
+    need = sum(4 * (hi[y] - (lo[y] & ~3) + 1) for y in lo)
+    assert need <= traffic <= need + 4 * 12 * len(lo) + 4 * 12 * 4
+    assert traffic < box

@@ -429,15 +429,18 @@ def test_4k_bench_configuration_sampled():
 # ------------------------------------------------------------------ host frames -> disk boxes
 @pytest.mark.parametrize("pinned", [True, False])
 def test_upload_disk_boxes_give_the_same_moments(pinned):
-    """zm_upload_disk copies only the disk's bounding box (plus the bilinear
-    margin) of host frames; moments from the boxes match moments from the whole
-    frames on the device (float rounding of the shifted coordinates only)."""
+    """zm_upload_disk copies only the disk's row spans (plus the bilinear
+    margin) of host frames into their bounding boxes; moments from the boxes
+    match moments from the whole frames on the device (float rounding of the
+    shifted coordinates only).  The device buffer starts as NaN, so a pixel
+    read outside the copied spans would show in the moments."""
     frames = [synth.blob_image(270, 480, 6, workload=70, index=b) for b in range(3)]
     geos = [None, (250.0, 140.0, 100.0), (20.5, 30.0, 60.0)]      # centred, off-centre, clipped by the edge
     host = [torch.from_numpy(f).pin_memory() if pinned else torch.from_numpy(f) for f in frames]
     with Plan(40, 64, 128, zm.ZM_PREC_BF16X3) as p:
         nbytes = zm.zm_upload_disk_bytes(host, geometries=geos)
-        dev_buf = torch.empty(nbytes // 4 + 4, device=DEV)
+        assert zm.zm_upload_disk_traffic(host, geometries=geos) < nbytes
+        dev_buf = torch.full((nbytes // 4 + 4,), float("nan"), device=DEV)
         try:
             boxes = zm.zm_upload_disk(host, dev_buf, geometries=geos)
         except zm.ZmError as e:                                  # pageable memory on a device that cannot read it
