@@ -390,6 +390,7 @@ def run_gb300(args):
         torch.cuda.empty_cache()
         img0, frame0 = line.pop("_frame0")
         line["uneven_batch"] = bench_uneven(zm, torch, dev)
+        line["stability"] = bench_stability(zm, torch, dev)
         line["serving"] = bench_serving(zm)
         line["cpu_baseline"], Zref = cpu_baseline(img0)
         line["err_vs_fp64"] = {k: float(np.max(np.abs(z - Zref)) / np.max(np.abs(Zref))) for k, z in frame0.items()}
@@ -506,6 +507,36 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
                   "steps": reps,
                   "h2d": "row spans of the disks of the pinned frames, read by a kernel (zm_upload_disk), "
                          "the next step's upload overlapping this step's compute"}
+    return res
+
+
+def bench_stability(zm, torch, dev):
+    """Reconstruction error vs order up to n_max = 500 (the paper's stability
+    range, Sec. 3.1): one 1024x1024 blob frame, moments with the Eq. 7 table on
+    Gauss-Legendre and midpoint radial nodes, reconstruction on the polar nodes
+    (Neumann), Eq. 10 / Eq. 13 errors; plan build time per order."""
+    from paper_2304_14492_gb300 import synth
+    size, n_rho, n_theta = 1024, 512, 1024
+    img = torch.from_numpy(synth.blob_image(size, size, 16, workload=5, index=0)).to(dev)
+    res = {"frame": "1024x1024 blob frame, disk d=1024 centred", "n_rho": n_rho, "n_theta": n_theta, "rows": []}
+    for gname, gflag in (("gauss", zm.ZM_GRID_GAUSS), ("midpoint", zm.ZM_GRID_MIDPOINT)):
+        for pname, pflag in (("fp32", zm.ZM_PREC_FP32), ("bf16x3", zm.ZM_PREC_BF16X3)):
+            for n_max in (25, 50, 100, 200, 300, 400, 500):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                plan = zm.zm_plan(n_max, n_rho, n_theta, gflag | pflag)
+                torch.cuda.synchronize(dev)
+                plan_ms = 1000 * (time.perf_counter() - t0)
+                P = zm.zm_num_moments(n_max)
+                out = torch.empty((1, P, 2), device=dev)
+                fh = torch.empty((1, n_rho, n_theta), device=dev)
+                err = torch.empty((1, 4), device=dev, dtype=torch.float64)
+                zm.zm_moments_ex(plan, [img], out, fh)
+                zm.zm_reconstruct_errors(plan, out, 1, None, fh, err, zm.ZM_NEUMANN)
+                e = err.cpu().numpy()[0]
+                zm.zm_plan_destroy(plan)
+                res["rows"].append({"grid": gname, "precision": pname, "n_max": n_max, "eps1": float(e[0]),
+                                    "eps": float(e[1]), "plan_ms": plan_ms})
     return res
 
 

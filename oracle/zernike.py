@@ -70,6 +70,13 @@ def _jacobi_0b(s_max, beta, x):
     return out
 
 
+def zrp(n, m, rho):
+    """R_n^m(rho) for one pair, by the same recurrence as zrp_table (the table's
+    row for (n, m) without the other rows)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return rho ** m * _jacobi_0b((n - m) // 2, float(m), 2.0 * rho * rho - 1.0)[(n - m) // 2]
+
+
 def zrp_table(n_max, rho):
     """R_nm(rho_i) for every stored (n, m) up to n_max, float64.
 

@@ -458,3 +458,47 @@ def test_upload_disk_boxes_give_the_same_moments(pinned):
         ref = om.moments(frames[b].astype(np.float64), 40, 64, 128,
                          geometry=geos[b] if geos[b] else None)
         assert metrics.rel_max_err(g[b], ref) <= TOL_Z, b
+
+
+# ------------------------------------------------------------------ high orders on Gauss-Legendre nodes
+@pytest.mark.parametrize("prec", [zm.ZM_PREC_FP32, zm.ZM_PREC_BF16X3])
+@pytest.mark.parametrize("npr,mpr", [(480, 40), (497, 1), (500, 500), (300, 0)])
+def test_high_order_polar_closed_form(prec, npr, mpr):
+    """Orders up to 500 (the paper's stability range, Sec. 3.1): the polar input
+    R_{n'm'}(rho) cos(m' theta) on Gauss-Legendre nodes has the closed-form
+    moments 1 (m' = 0) or 1/2 at (n', m') and 0 elsewhere; the table comes from
+    Eq. 7, the input from the oracle's Jacobi recurrence."""
+    n_max, n_rho, n_theta = 500, 512, 1024
+    rho, _ = grid.radial_nodes(n_rho, "gauss")
+    th = grid.angles(n_theta)
+    R = zernike.zrp(npr, mpr, rho)
+    fh = dev((R[:, None] * np.cos(mpr * th)[None, :])[None])
+    with Plan(n_max, n_rho, n_theta, prec | zm.ZM_GRID_GAUSS) as p:
+        out = torch.empty((1, p.P, 2), device=DEV)
+        zm.zm_moments_polar(p.h, fh, 1, out)
+        torch.cuda.synchronize()
+        Z = as_complex(out)[0]
+    want = np.zeros(p.P, complex)
+    want[zernike.moment_index(npr, mpr)] = 1.0 if mpr == 0 else 0.5
+    assert np.max(np.abs(Z - want)) <= (2e-5 if prec == zm.ZM_PREC_FP32 else 1e-4)
+
+
+def test_reconstruction_error_does_not_grow_with_order_on_gauss_nodes():
+    """With Gauss-Legendre radial nodes (N_rho >= n_max + 1) the discrete
+    Zernike functions are orthogonal on the grid, so the reconstruction is a
+    projection onto a growing subspace and its error (Eq. 10, Eq. 13 on the
+    polar nodes) cannot grow with n_max: no high-order breakdown (Sec. 3.1)."""
+    img = synth.blob_image(512, 512, 12, workload=71, index=0)
+    n_rho, n_theta = 320, 1024
+    eps = []
+    for n_max in (20, 60, 120, 200, 300):
+        with Plan(n_max, n_rho, n_theta, zm.ZM_PREC_FP32 | zm.ZM_GRID_GAUSS) as p:
+            out = torch.empty((1, p.P, 2), device=DEV)
+            fh = torch.empty((1, n_rho, n_theta), device=DEV)
+            zm.zm_moments_ex(p.h, [dev(img)], out, fh)
+            err = torch.empty((1, 4), device=DEV, dtype=torch.float64)
+            zm.zm_reconstruct_errors(p.h, out, 1, None, fh, err, zm.ZM_NEUMANN)
+            torch.cuda.synchronize()
+            eps.append(float(err[0, 0]))
+    assert all(b <= a * (1 + 1e-3) for a, b in zip(eps, eps[1:])), eps
+    assert eps[-1] < 0.5 * eps[0], eps

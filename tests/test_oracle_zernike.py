@@ -91,6 +91,15 @@ def test_recurrence_vs_exact_high_order(n, m):
         assert abs(table[row, j] - float(exact)) <= 1e-13
 
 
+@pytest.mark.parametrize("n,m", [(0, 0), (7, 3), (100, 36), (500, 10), (500, 500), (499, 1)])
+def test_single_pair_vs_exact(n, m):
+    # zrp(n, m, .) against the exact rational Eq. 2 at dyadic nodes
+    rhos = [Fraction(255, 256), Fraction(1, 2), Fraction(1, 1024), Fraction(701, 1024), Fraction(1)]
+    got = zernike.zrp(n, m, np.array([float(r) for r in rhos]))
+    for j, r in enumerate(rhos):
+        assert abs(got[j] - float(zernike.zrp_exact(n, m, r))) <= 1e-13
+
+
 def test_recurrence_vs_scipy_jacobi_and_legendre():
     rho = np.linspace(0.0, 1.0, 57)
     n_max = 40
