@@ -386,6 +386,7 @@ def run_gb300(args):
 
     if rank == 0 and not args.quick:
         line.update(extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P))
+        line["colour"] = bench_colour(zm, torch, dev, plan, P)
         del views, imgs
         torch.cuda.empty_cache()
         img0, frame0 = line.pop("_frame0")
@@ -538,6 +539,46 @@ def bench_stability(zm, torch, dev):
                 res["rows"].append({"grid": gname, "precision": pname, "n_max": n_max, "eps1": float(e[0]),
                                     "eps": float(e[1]), "plan_ms": plan_ms})
     return res
+
+
+def bench_colour(zm, torch, dev, plan, P, steps=20):
+    """One 4K colour frame as a batch of its three bands (Sec. 2.3, Sec. 3):
+    per-band min / max over the disk, moments, Cartesian reconstruction (Neumann),
+    min-max normalisation to each band's stored range (Table I), Eq. 10 / Eq. 13
+    per band; colour frames/s with the bands resident on the device."""
+    from paper_2304_14492_gb300 import synth
+    bands = [torch.from_numpy(synth.blob_image(H, W, N_BLOBS, workload=SYNTH_WORKLOAD_ID, index=1000 + c)).to(dev)
+             for c in range(3)]
+    descs = zm.image_array(bands)
+    canv = [torch.empty((H, W), device=dev) for _ in range(3)]
+    cdescs, tdescs = zm.canvas_array(canv), zm.image_array(canv)
+    mm = torch.empty((3, 2), device=dev)
+    out = torch.empty((3, P, 2), device=dev)
+    polar = torch.empty((3, N_RHO, N_THETA), device=dev)
+    err = torch.empty((3, 4), device=dev, dtype=torch.float64)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        zm.zm_disk_minmax(plan, descs, mm, st)
+        zm.zm_moments(plan, descs, out, 0, st)
+        zm.zm_reconstruct_cartesian(plan, out, cdescs, polar, zm.ZM_NEUMANN, st)
+        zm.zm_minmax_normalize(plan, cdescs, mm, st)
+        zm.zm_errors(plan, descs, tdescs, err, st)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    e = err.cpu().numpy()
+    return {"frame": "3 bands of 3840x2160 blob frames, n_max=100, N_rho=N_theta=1024", "ms_per_frame": ms,
+            "frames_per_s": 1000.0 / ms, "eps1_per_band": [float(x) for x in e[:, 0]],
+            "eps13_per_band": [float(x) for x in e[:, 1]]}
 
 
 def bench_uneven(zm, torch, dev, count=256):

@@ -202,7 +202,15 @@ def _images(imgs, geometries=None):
     return arr, len(imgs)
 
 
+def canvas_array(canvases, geometries=None):
+    """The zm_canvas_t array of a list of 2-D float32 CUDA tensors, to be built
+    once and passed to the canvas entry points in place of the list."""
+    return _canvases(canvases, geometries)[0]
+
+
 def _canvases(cvs, geometries=None):
+    if isinstance(cvs, ctypes.Array):
+        return cvs, len(cvs)
     cvs = list(cvs)
     geos = list(geometries) if geometries is not None else [None] * len(cvs)
     arr = (zm_canvas_t * len(cvs))(*[canvas_desc(t, g) for t, g in zip(cvs, geos)])

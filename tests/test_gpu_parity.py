@@ -502,3 +502,49 @@ def test_reconstruction_error_does_not_grow_with_order_on_gauss_nodes():
             eps.append(float(err[0, 0]))
     assert all(b <= a * (1 + 1e-3) for a, b in zip(eps, eps[1:])), eps
     assert eps[-1] < 0.5 * eps[0], eps
+
+
+# ------------------------------------------------------------------ colour frames (three bands)
+def test_colour_frame_as_three_bands_matches_oracle():
+    """A colour frame is a batch of its three bands (Sec. 2.3, Sec. 3): per-band
+    min / max over the disk kept, moments and the Cartesian reconstruction of
+    each band, the reconstruction min-max normalised to its band's stored range
+    (Table I), and Eq. 10 / Eq. 13 per band."""
+    h, w = 64, 80
+    bands = [synth.blob_image(h, w, 4 + c, workload=72, index=c) * (0.5 + 0.25 * c) for c in range(3)]
+    n_max, n_rho, n_theta = 20, 32, 64
+    mask = metrics.disk_mask(h, w)
+    with Plan(n_max, n_rho, n_theta) as p:
+        db = [dev(b) for b in bands]
+        mm = torch.empty((3, 2), device=DEV)
+        zm.zm_disk_minmax(p.h, db, mm)
+        out = torch.empty((3, p.P, 2), device=DEV)
+        zm.zm_moments(p.h, db, out)
+        canv = [torch.zeros((h, w), device=DEV) for _ in range(3)]
+        polar = torch.empty((3, n_rho, n_theta), device=DEV)
+        zm.zm_reconstruct_cartesian(p.h, out, canv, polar, zm.ZM_NEUMANN)
+        zm.zm_minmax_normalize(p.h, canv, mm)
+        err = torch.empty((3, 4), device=DEV, dtype=torch.float64)
+        zm.zm_errors(p.h, db, canv, err)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+    rho, _ = grid.radial_nodes(n_rho)
+    geo = grid.default_geometry(h, w)
+    y, x = np.mgrid[0:h, 0:w]
+    r_xy, _ = grid.pixel_to_polar(x, y, geo)
+    inner = mask & (np.abs(r_xy - 1.0) > 1e-5)
+    for c in range(3):
+        f = bands[c].astype(np.float64)
+        lo, hi = f[mask].min(), f[mask].max()
+        assert abs(float(mm[c, 0]) - lo) <= 1e-6 and abs(float(mm[c, 1]) - hi) <= 1e-6
+        Zref = oracle_moments(bands[c], p)
+        assert metrics.rel_max_err(Z[c], Zref) <= TOL_Z
+        polar_ref = orc.reconstruct_polar(Zref, n_max, n_rho, n_theta, neumann=True)
+        ref = metrics.minmax_normalize(orc.polar_to_cartesian(polar_ref, rho, h, w), lo, hi, mask)
+        got = canv[c].double().cpu().numpy()
+        assert np.max(np.abs(got[inner] - ref[inner])) <= 1e-3 * (hi - lo), c
+        e = err[c].cpu().numpy()
+        # the errors of the GPU's own normalised band, and against the oracle's
+        assert abs(e[0] - metrics.eps1(f, got, mask)) <= 1e-4 * e[0]
+        assert abs(e[1] - metrics.eps13(f, got, mask)) <= 1e-4 * e[1]
+        assert abs(e[1] - metrics.eps13(f, ref, mask)) <= 5e-2 * e[1]
