@@ -392,6 +392,7 @@ def run_gb300(args):
         img0, frame0 = line.pop("_frame0")
         line["uneven_batch"] = bench_uneven(zm, torch, dev)
         line["stability"] = bench_stability(zm, torch, dev)
+        line["cartesian"] = bench_cartesian(zm, torch, dev)
         line["serving"] = bench_serving(zm)
         line["cpu_baseline"], Zref = cpu_baseline(img0)
         line["err_vs_fp64"] = {k: float(np.max(np.abs(z - Zref)) / np.max(np.abs(Zref))) for k, z in frame0.items()}
@@ -579,6 +580,58 @@ def bench_colour(zm, torch, dev, plan, P, steps=20):
     return {"frame": "3 bands of 3840x2160 blob frames, n_max=100, N_rho=N_theta=1024", "ms_per_frame": ms,
             "frames_per_s": 1000.0 / ms, "eps1_per_band": [float(x) for x in e[:, 0]],
             "eps13_per_band": [float(x) for x in e[:, 1]]}
+
+
+def bench_cartesian(zm, torch, dev, reps=50):
+    """Cartesian summation (Eq. 3-6) with 8-point symmetry, the paper's Fig. 5
+    mode: one moment of a given order of one N x N frame (disk inscribed),
+    device time per moment; HBM roofline on the pixels of the disk read once."""
+    from paper_2304_14492_gb300 import synth
+    peaks = {}
+    try:
+        import json as _json
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    st = torch.cuda.current_stream(dev)
+    out = torch.empty((1, 1, 2), device=dev)
+    work = torch.empty(zm.zm_cartesian_work_bytes(1, 1) // 8 + 1, dtype=torch.float64, device=dev)
+    rows = []
+    for size in (1000, 2000, 4000):
+        img = torch.from_numpy(synth.blob_image(size, size, 24, workload=SYNTH_WORKLOAD_ID, index=2000 + size)).to(dev)
+        descs = zm.image_array([img])
+        disk_px = int(np.count_nonzero(
+            ((2 * np.arange(size) + 1 - size)[None, :] ** 2 + (2 * np.arange(size) + 1 - size)[:, None] ** 2)
+            <= size * size))
+        for (n, m) in ((100, 36), (20, 0), (400, 2)):
+            for _ in range(3):
+                zm.zm_cartesian_moments(descs, [(n, m)], out, work, 0, st)
+            torch.cuda.synchronize(dev)
+            # `reps` calls captured in a CUDA graph: device time per call, not
+            # the Python marshalling of each call
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                cs = torch.cuda.current_stream(dev)
+                for _ in range(reps):
+                    zm.zm_cartesian_moments(descs, [(n, m)], out, work, 0, cs)
+            graph.replay()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            graph.replay()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            del graph
+            gbs = disk_px * 4 / (ms / 1000.0) / 1e9
+            rows.append({"N": size, "n": n, "m": m, "ms_per_moment": ms, "moments_per_s": 1000.0 / ms,
+                         "disk_bytes": disk_px * 4, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm})
+        del img
+    return {"mode": "one moment of one N x N blob frame per call, inscribed disk, 8-point symmetry, fp32",
+            "note": "the paper's Fig. 5 reports about 20 frames/s (50 ms per moment) at 4000 x 4000 on a "
+                    "Titan Xp; context only (another GPU)",
+            "rows": rows}
 
 
 def bench_uneven(zm, torch, dev, count=256):

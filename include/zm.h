@@ -187,6 +187,27 @@ int zm_upload_disk_traffic(const zm_image_t* host_imgs, int batch, unsigned long
 int zm_upload_disk(const zm_image_t* host_imgs, int batch, float* dev, unsigned long long dev_bytes,
                    zm_image_t* dev_imgs, void* stream);
 
+/*
+ * Zernike moments by Cartesian summation (Sec. 2, Eq. 3-6; the route of the
+ * paper's Fig. 5 timings): for each image b and each requested pair
+ * (n, m) = (nm[2k], nm[2k+1]) (host int[count][2], m >= 0, n - m even,
+ * (n - m)/2 < 512),
+ *   out[b][k] = (n + 1)/(pi r^2) sum f(x, y) R_nm(rho) e^{-j m theta}
+ * over the pixel centres with x^2 + y^2 <= 1, x = (col - cx)/r,
+ * y = (cy - row)/r (the polar path's geometry; the pixel area 1/r^2 is
+ * Delta^2 of Eq. 5, i.e. 4/N^2 for an N x N image), divided by eps_m with
+ * ZM_NEUMANN.  No interpolation.  When cx and cy sit at the same offset, 0 or
+ * 1/2, from the pixel grid (the centred default always does), the pixels are
+ * taken in orbits of the 8-point symmetry.  `imgs`: device images (host array
+ * of descriptors); `out`: device float[batch][count][2]; `work`: device
+ * scratch of zm_cartesian_work_bytes() bytes, 8-byte aligned; asynchronous on
+ * `stream`.  ZM_EINVAL for a bad pair, NULL pointers or a short `work`.
+ */
+int zm_cartesian_work_bytes(int batch, int count, unsigned long long* bytes);
+int zm_cartesian_moments(const zm_image_t* imgs, int batch, const int* nm, int count,
+                         float* out, void* work, unsigned long long work_bytes,
+                         unsigned flags, void* stream);
+
 /* Only the bilinear polar resampling (Sec. 2.5): fhat = device
  * float[batch][N_rho][N_theta]. */
 int zm_resample(zm_plan_t plan, const zm_image_t* imgs, int batch, float* fhat,

@@ -79,6 +79,9 @@ SIGNATURES = {
     "zm_moments_polar": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_upload_disk_bytes": (c_int, [c_void_p, c_int, POINTER(ctypes.c_ulonglong)]),
     "zm_upload_disk_traffic": (c_int, [c_void_p, c_int, POINTER(ctypes.c_ulonglong)]),
+    "zm_cartesian_work_bytes": (c_int, [c_int, c_int, POINTER(ctypes.c_ulonglong)]),
+    "zm_cartesian_moments": (c_int, [POINTER(zm_image_t), c_int, POINTER(c_int), c_int, c_void_p, c_void_p,
+                                     ctypes.c_ulonglong, c_uint, c_void_p]),
     "zm_upload_disk": (c_int, [c_void_p, c_int, c_void_p, ctypes.c_ulonglong, c_void_p, c_void_p]),
     "zm_resample": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p]),
     "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
@@ -292,6 +295,24 @@ def zm_upload_disk_bytes(host_images, geometries=None):
     b = ctypes.c_ulonglong()
     _check(lib().zm_upload_disk_bytes(arr, n, ctypes.byref(b)))
     return b.value
+
+
+def zm_cartesian_work_bytes(batch, count):
+    b = ctypes.c_ulonglong()
+    _check(lib().zm_cartesian_work_bytes(batch, count, ctypes.byref(b)))
+    return b.value
+
+
+def zm_cartesian_moments(images, pairs, out, work, flags=0, stream=None, geometries=None):
+    """Moments (n, m) in `pairs` by Cartesian summation (Eq. 6) into the device
+    tensor out[batch][len(pairs)][2]; `work` a device tensor of at least
+    zm_cartesian_work_bytes(batch, len(pairs)) bytes."""
+    arr, n = _images(images, geometries)
+    pairs = list(pairs)
+    nm = (c_int * (2 * len(pairs)))(*[v for pr in pairs for v in pr])
+    nbytes = work.numel() * work.element_size()
+    _check(lib().zm_cartesian_moments(arr, n, nm, len(pairs), _ptr(out), _ptr(work), nbytes, flags,
+                                      _stream(stream)))
 
 
 def zm_upload_disk_traffic(host_images, geometries=None):

@@ -548,3 +548,77 @@ def test_colour_frame_as_three_bands_matches_oracle():
         assert abs(e[0] - metrics.eps1(f, got, mask)) <= 1e-4 * e[0]
         assert abs(e[1] - metrics.eps13(f, got, mask)) <= 1e-4 * e[1]
         assert abs(e[1] - metrics.eps13(f, ref, mask)) <= 5e-2 * e[1]
+
+
+# ------------------------------------------------------------------ Cartesian summation (Eq. 3-6)
+from oracle import cartesian as ocart  # noqa: E402
+
+CART_PAIRS = [(0, 0), (1, 1), (2, 0), (5, 3), (20, 12), (40, 40), (37, 1), (63, 59), (100, 6)]
+
+
+def cart_gpu(imgs, pairs, geos=None, flags=0):
+    ts = [dev(i) for i in imgs]
+    out = torch.empty((len(ts), len(pairs), 2), device=DEV)
+    work = torch.empty(zm.zm_cartesian_work_bytes(len(ts), len(pairs)) // 8 + 1, dtype=torch.float64, device=DEV)
+    zm.zm_cartesian_moments(ts, pairs, out, work, flags, geometries=geos)
+    torch.cuda.synchronize()
+    return as_complex(out)
+
+
+def cart_bound(img, geo, n):
+    # |R e^{-j m theta}| <= 1: the moment's natural scale, for FP32 rounding
+    rows, cols, _, _ = ocart.disk_pixels(*img.shape, geo)
+    return (n + 1) / (np.pi * geo[2] ** 2) * np.sum(np.abs(img[rows, cols]))
+
+
+@pytest.mark.parametrize("h,w,geo", [
+    (64, 64, None),                      # half offset: 8-point orbits
+    (63, 63, None),                      # integer offset: orbits with v = 0 and u = v
+    (60, 75, None),                      # cx integer, cy half: one thread per pixel
+    (50, 70, (30.5, 20.5, 18.0)),        # explicit disk inside the image
+    (40, 40, (10.5, 12.5, 30.0)),        # disk reaching past the edges (zero outside)
+    (45, 52, (20.3, 21.7, 15.5))])       # off-grid centre: per pixel
+def test_cartesian_matches_oracle(h, w, geo):
+    img = synth.blob_image(h, w, 5, workload=73, index=h + w)
+    got = cart_gpu([img], CART_PAIRS, [geo] if geo else None)[0]
+    g = geo if geo else grid.default_geometry(h, w)
+    ref = ocart.moments_cartesian(img, CART_PAIRS, g)
+    for k, (n, m) in enumerate(CART_PAIRS):
+        assert abs(got[k] - ref[k]) <= 2e-6 * cart_bound(img.astype(np.float64), g, n), (n, m, got[k], ref[k])
+
+
+def test_cartesian_batches_pairs_and_neumann():
+    imgs = [synth.blob_image(48 + 2 * b, 48 + 2 * b, 4, workload=74, index=b) for b in range(10)]
+    pairs = [(4, 0), (7, 3), (12, 8), (9, 1), (30, 0), (2, 2)]
+    plain = cart_gpu(imgs, pairs)
+    neu = cart_gpu(imgs, pairs, flags=zm.ZM_NEUMANN)
+    for b, img in enumerate(imgs):
+        ref = ocart.moments_cartesian(img, pairs)
+        g = grid.default_geometry(*img.shape)
+        for k, (n, m) in enumerate(pairs):
+            tol = 2e-6 * cart_bound(img.astype(np.float64), g, n)
+            assert abs(plain[b, k] - ref[k]) <= tol
+            assert abs(neu[b, k] - ref[k] / (2.0 if m == 0 else 1.0)) <= tol
+
+
+def test_cartesian_large_frame_single_moment():
+    img = synth.blob_image(2048, 2048, 24, workload=75, index=0)
+    pairs = [(100, 36), (99, 1)]
+    got = cart_gpu([img], pairs)[0]
+    ref = ocart.moments_cartesian(img, pairs)
+    g = grid.default_geometry(2048, 2048)
+    for k, (n, m) in enumerate(pairs):
+        assert abs(got[k] - ref[k]) <= 2e-6 * cart_bound(img.astype(np.float64), g, n)
+
+
+def test_cartesian_argument_errors():
+    img = dev(np.ones((16, 16), np.float32))
+    out = torch.empty((1, 1, 2), device=DEV)
+    work = torch.empty(zm.zm_cartesian_work_bytes(1, 1) // 8 + 1, dtype=torch.float64, device=DEV)
+    for bad in ([(3, 2)], [(2, 3)], [(-1, 1)], [(1030, 0)]):
+        with pytest.raises(zm.ZmError) as e:
+            zm.zm_cartesian_moments([img], bad, out, work)
+        assert e.value.status == zm.ZM_EINVAL
+    with pytest.raises(zm.ZmError) as e:
+        zm.zm_cartesian_moments([img], [(2, 0)], out, work[:2])
+    assert e.value.status == zm.ZM_EINVAL
