@@ -385,6 +385,7 @@ def run_gb300(args):
             "roofline": roofline, "gpu_launches": l1 - l0, "clocks": clocks, "plan_ms": plan_ms}
 
     if rank == 0 and not args.quick:
+        line["pipelined"] = bench_pipelined(zm, torch, dev, descs, B, P)
         line.update(extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P))
         line["colour"] = bench_colour(zm, torch, dev, plan, P)
         del views, imgs
@@ -510,6 +511,52 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
                   "h2d": "row spans of the disks of the pinned frames, read by a kernel (zm_upload_disk), "
                          "the next step's upload overlapping this step's compute"}
     return res
+
+
+def bench_pipelined(zm, torch, dev, descs, B, P, pipelines=2, batches=200):
+    """The same step on `pipelines` independent pipelines (plan, buffers and
+    stream each), batches dealt round-robin: the memory-bound resampler of one
+    batch overlaps the issue-bound ring FFTs of another.  Whole-job frames/s;
+    the headline stays the one-stream step, whose kernel timings the roofline
+    needs."""
+    pipes = []
+    for _ in range(pipelines):
+        plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
+        zm.zm_plan_reserve(plan, B)
+        pipes.append({"plan": plan, "st": torch.cuda.Stream(dev),
+                      "fhat": torch.empty((B, N_RHO, N_THETA), device=dev),
+                      "out": torch.empty((B, P, 2), device=dev),
+                      "frec": torch.empty((B, N_RHO, N_THETA), device=dev),
+                      "err": torch.empty((B, 4), device=dev, dtype=torch.float64)})
+
+    def step(q):
+        zm.zm_resample(q["plan"], descs, q["fhat"], q["st"])
+        zm.zm_moments_polar(q["plan"], q["fhat"], B, q["out"], 0, q["st"])
+        zm.zm_reconstruct_errors(q["plan"], q["out"], B, q["frec"], q["fhat"], q["err"], zm.ZM_NEUMANN, q["st"])
+
+    for k in range(4 * pipelines):
+        step(pipes[k % pipelines])
+    torch.cuda.synchronize(dev)
+    main = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for q in pipes:
+        q["st"].wait_event(e0)
+    for k in range(batches):
+        step(pipes[k % pipelines])
+    for q in pipes:
+        ev = torch.cuda.Event()
+        ev.record(q["st"])
+        main.wait_event(ev)
+    e1.record(main)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    for q in pipes:
+        zm.zm_plan_destroy(q["plan"])
+    return {"pipelines": pipelines, "batches": batches, "batch": B, "ms_per_batch": ms / batches,
+            "images_per_s": B * batches / (ms / 1000.0),
+            "note": "the step of the headline on %d streams at once (a plan and buffers each), batches "
+                    "dealt round-robin" % pipelines}
 
 
 def bench_stability(zm, torch, dev):
