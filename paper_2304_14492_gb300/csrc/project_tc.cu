@@ -714,9 +714,14 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
     if (split) {
         cudaError_t e = launch_pdl_cluster(k_project_blk, dim3(p->n_max + 1, tiles, 2), dim3(TC_THREADS),
                                            dim3(1, 1, 2), smem, st, bp);
-        if (e != cudaSuccess) return cuda_error(e, "k_project_blk");
-        count_launch();
-        return ZM_OK;
+        if (e == cudaSuccess) {
+            count_launch();
+            return ZM_OK;
+        }
+        // a device or partition that cannot place the pairs: the same stages,
+        // one CTA per order over the whole radial range
+        cudaGetLastError();
+        bp.ksplit = 1;
     }
     ZM_LAUNCH_PDL("k_project_blk", k_project_blk, dim3(p->n_max + 1, tiles), dim3(TC_THREADS), smem, st, bp);
     return ZM_OK;
