@@ -350,6 +350,8 @@ int build_plan_tables(zm_plan_t p) {
     ZM_CUDA_TRY(cudaMalloc(&p->mrow, sizeof(int) * (p->n_max + 2)));
     ZM_CUDA_TRY(cudaMalloc(&p->status, sizeof(int)));
     ZM_CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    ZM_CUDA_TRY(cudaMalloc(&p->work, 2 * sizeof(int)));
+    ZM_CUDA_TRY(cudaMemset(p->work, 0, 2 * sizeof(int)));
     ZM_CUDA_TRY(cudaMalloc(&p->pair_nm, sizeof(int2) * P));
     ZM_CUDA_TRY(cudaMemcpy(p->mrow, p->mrow_h.data(), sizeof(int) * (p->n_max + 2), cudaMemcpyHostToDevice));
     ZM_CUDA_TRY(cudaMemcpy(p->pair_nm, pairs.data(), sizeof(int2) * P, cudaMemcpyHostToDevice));
@@ -401,6 +403,7 @@ static void free_plan(zm_plan_t p) {
     cudaFree(p->mrow);
     cudaFree(p->pair_nm);
     cudaFree(p->status);
+    cudaFree(p->work);
     delete p;
 }
 

@@ -88,7 +88,10 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 // order the inverse FFT wants, and its output is already in natural order
 // across lanes, so f~ is written (and the reference read) with coalesced
 // accesses from registers.  The grid is persistent: each CTA loads the
-// twiddles once and walks blocks of R rings (b, rb).
+// twiddles once and takes blocks of R rings (b, rb): first item blockIdx.x,
+// then items claimed from the counter work[0] (dynamic, so that the CTAs
+// finish within about one item of each other); the last CTA to finish sets
+// work[0..1] back to 0 for the next launch.
 // With ERR, each warp also accumulates, against the reference polar samples
 // `ref`, sum (ref - f~)^2, sum ref^2 and max ref of its ring into one record
 // part[b][i] = (sd, sf, max, 0) (Eq. 10 / Eq. 13 on the polar nodes); `out`
@@ -96,7 +99,8 @@ k_recon_radial(const float* __restrict__ R32m, const float2* __restrict__ Z, con
 template <int LOGN, bool ERR>
 __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4))
 k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_max, int n_rho, int batch,
-             float* __restrict__ out, const float* __restrict__ ref, float4* __restrict__ part) {
+             float* __restrict__ out, const float* __restrict__ ref, float4* __restrict__ part,
+             int* __restrict__ work) {
     using FFT = RingFFT<LOGN>;
     constexpr int N = FFT::N;
     constexpr int M = FFT::M;
@@ -114,8 +118,10 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
     griddep_wait();                    // G (and the reference samples) are written, out is free
     griddep_launch();
     // persistent: the CTA takes ring blocks (b, rb) = item / n_rb, item mod n_rb
+    __shared__ int next_item;
     const int n_rb = (n_rho + R - 1) / R;
-    for (int item = blockIdx.x; item < n_rb * batch; item += gridDim.x) {
+    const int n_items = n_rb * batch;
+    for (int item = blockIdx.x; item < n_items;) {
         const int b = item / n_rb, rb = item - b * n_rb;
         const int i0 = rb * R;
         // this block's G is one contiguous run of nm1 x 16 floats (g_index)
@@ -205,7 +211,20 @@ k_recon_ifft(const float* __restrict__ G, const float2* __restrict__ tw, int n_m
             }
             if (lane == 0 && i < n_rho) part[(size_t)b * n_rho + i] = make_float4(sd, sf, mx, 0.f);
         }
-        __syncthreads();   // Gs is refilled for the next ring block
+        if (threadIdx.x == 0) next_item = (int)gridDim.x + atomicAdd(&work[0], 1);
+        __syncthreads();   // Gs is refilled for the next ring block; next_item is set
+        item = next_item;
+        __syncthreads();   // every thread has read next_item before it is rewritten
+    }
+    // the last CTA out resets the counter (every CTA's last claim precedes its
+    // arrival here)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1) == (int)gridDim.x - 1) {
+            work[0] = 0;
+            work[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -226,7 +245,7 @@ static int resident_blocks(K kernel, int threads, size_t smem) {
 
 template <int LOGN, bool ERR>
 static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho, int batch, float* out,
-                         const float* ref, float4* part, int sms, cudaStream_t st) {
+                         const float* ref, float4* part, int* work, int sms, cudaStream_t st) {
     using FFT = RingFFT<LOGN>;
     const int R = 8;
     const size_t smem = sizeof(float2) * ((size_t)R * (n_max + 1) + FFT::TW_FLOAT2 + FFT::M + (size_t)R * FFT::TBUF);
@@ -242,7 +261,7 @@ static int launch_ifft_t(const float* G, const float2* tw, int n_max, int n_rho,
     const int slots = sms * resident_blocks(k_recon_ifft<LOGN, ERR>, R * 32, smem);
     const int grid = (int)std::min<long long>(items, slots);
     ZM_LAUNCH_PDL("k_recon_ifft", (k_recon_ifft<LOGN, ERR>), dim3(grid), dim3(R * 32), smem, st, G, tw, n_max, n_rho,
-                  batch, out, ref, part);
+                  batch, out, ref, part, work);
     return ZM_OK;
 }
 
@@ -257,15 +276,15 @@ static int launch_ifft(zm_plan_t p, const float* G, int batch, float* out, const
         if (dev >= 0 && dev < 64) sms_cache[dev] = sms;
     }
     switch (p->log_theta) {
-        case 3: return launch_ifft_t<3, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 4: return launch_ifft_t<4, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 5: return launch_ifft_t<5, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 6: return launch_ifft_t<6, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 7: return launch_ifft_t<7, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 8: return launch_ifft_t<8, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 9: return launch_ifft_t<9, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 10: return launch_ifft_t<10, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
-        case 11: return launch_ifft_t<11, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, sms, st);
+        case 3: return launch_ifft_t<3, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 4: return launch_ifft_t<4, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 5: return launch_ifft_t<5, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 6: return launch_ifft_t<6, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 7: return launch_ifft_t<7, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 8: return launch_ifft_t<8, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 9: return launch_ifft_t<9, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 10: return launch_ifft_t<10, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
+        case 11: return launch_ifft_t<11, ERR>(G, p->tw, p->n_max, p->n_rho, batch, out, ref, part, p->work, sms, st);
         default: return set_error(ZM_EUNSUPPORTED, "n_theta 2^%d", p->log_theta);
     }
 }

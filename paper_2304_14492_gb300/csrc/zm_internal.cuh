@@ -193,6 +193,7 @@ struct zm_plan_s {
     zm::Workspace ws_colmax;    // per-column max |F| (fp16 split scaling)
     zm::Workspace ws_Fblk;      // ring spectra as bf16 hi / lo operand blocks (blocked projection)
     int* status = nullptr;      // device status word: ZM_ETIMEOUT after a timed-out wait
+    int* work = nullptr;        // device {next item, CTAs done} of the inverse ring FFT, 0 between launches
     // launch choices
     int kb_rings = 8;           // rings per CTA in the resample + FFT kernel
     // set by the batch autotuner (0 = built-in heuristic)
