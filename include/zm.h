@@ -104,6 +104,9 @@ const char* zm_last_error(void);
  *  n_rho   in [1, 65536]
  *  n_theta a power of two in [8, 2048] with n_theta >= 2 n_max + 1
  *  flags   one ZM_GRID_* | one ZM_PREC_*
+ * The calls on one plan share its workspace and counters: order them (one
+ * stream, or streams joined by events); concurrent pipelines take one plan
+ * each.
  * Errors: ZM_EINVAL, ZM_ENOMEM, ZM_ECUDA, ZM_EUNSUPPORTED.
  */
 int zm_plan(zm_plan_t* plan, int n_max, int n_rho, int n_theta, unsigned flags);
