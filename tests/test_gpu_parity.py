@@ -622,3 +622,20 @@ def test_cartesian_argument_errors():
     with pytest.raises(zm.ZmError) as e:
         zm.zm_cartesian_moments([img], [(2, 0)], out, work[:2])
     assert e.value.status == zm.ZM_EINVAL
+
+
+@pytest.mark.parametrize("n_max,n_rho,n_theta", [(20, 32, 64), (100, 96, 1024), (500, 16, 2048), (3, 9, 8)])
+def test_ring_spectra_cross_check_against_cufft(n_max, n_rho, n_theta):
+    """The warp FFT's ring spectra against the vendor FFT (torch.fft on the
+    device, i.e. cuFFT) of the same polar samples: a cross-check only, the
+    product path never calls it."""
+    img = synth.blob_image(2 * n_rho + 4, 2 * n_rho + 2, 5, workload=76, index=n_theta)
+    with Plan(n_max, n_rho, n_theta) as p:
+        F = torch.empty((n_max + 1, 1, 2, n_rho), device=DEV)
+        fh = torch.empty((1, n_rho, n_theta), device=DEV)
+        zm.zm_ring_spectra(p.h, [dev(img)], F, fh)
+        ref = torch.fft.rfft(fh[0].double(), dim=-1)[:, : n_max + 1]          # [i][m], e^{-j m theta_k}
+        torch.cuda.synchronize()
+    got = torch.complex(F[:, 0, 0, :].double(), F[:, 0, 1, :].double()).T     # [i][m]
+    err = (got - ref).abs().max().item()
+    assert err <= 2e-6 * ref.abs().max().item() * np.log2(n_theta), err
