@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x3", "fp16x3"])
     ap.add_argument("--quick", action="store_true", help="skip latency / e2e / cpu-baseline extras")
+    ap.add_argument("--profile-pass", action="store_true",
+                    help="run every kernel path once at bench sizes (for a launch-list capture); no timing")
     return ap.parse_args()
 
 
@@ -780,10 +782,85 @@ def bench_serving(zm, rate=2000.0, seconds=10.0, seed=7):
             "note": "statistics reset after 16 plan-warming requests; latency = submit -> moments in host memory"}
 
 
+def profile_pass():
+    """Every kernel path of the library once, at the bench's sizes where it has
+    one: plan builds, the FP32 and FP16 projection forms on 16 4K frames, the
+    fused gather path (frames TMA cannot stage), the FP32 reconstruction with
+    errors, pixel reconstruction and normalisation (a colour frame), the upload
+    of host frames, the Cartesian route at 4000 x 4000, an uneven batch and a
+    few served requests.  For a launch-list capture under a profiler: prints
+    one line and measures nothing."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2304_14492_gb300 import native as zm, synth
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    B = 16
+    imgs = torch.from_numpy(np.stack(make_frames(B))).to(dev)
+    views = [imgs[b] for b in range(B)]
+    P = zm.zm_num_moments(N_MAX)
+    out = torch.empty((B, P, 2), device=dev)
+    fh = torch.empty((B, N_RHO, N_THETA), device=dev)
+    fr = torch.empty((B, N_RHO, N_THETA), device=dev)
+    err = torch.empty((B, 4), device=dev, dtype=torch.float64)
+    for prec in (zm.ZM_PREC_FP32, zm.ZM_PREC_FP16X3, zm.ZM_PREC_BF16X3):
+        plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, prec)
+        zm.zm_plan_reserve(plan, B)
+        zm.zm_moments_ex(plan, views, out, fh)
+        zm.zm_reconstruct_errors(plan, out, B, fr, fh, err, zm.ZM_NEUMANN)
+        if prec == zm.ZM_PREC_FP32:
+            # frames at a 4-byte offset: not TMA-eligible, the fused gather kernel
+            shifted = [imgs[b][:, 1:] for b in range(4)]
+            zm.zm_moments(plan, shifted, out[:4])
+            spectra = torch.empty((N_MAX + 1, 4, 2, N_RHO), device=dev)
+            zm.zm_ring_spectra(plan, views[:4], spectra, None)
+            zm.zm_project(plan, spectra, 4, out[:4])
+        torch.cuda.synchronize(dev)
+        zm.zm_plan_destroy(plan)
+    plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
+    bench_colour(zm, torch, dev, plan, P, steps=1)
+    zm.zm_plan_destroy(plan)
+    host = torch.empty((B, H, W), dtype=torch.float32, pin_memory=True)
+    host.copy_(imgs.cpu())
+    hv = [host[b] for b in range(B)]
+    dbuf = torch.empty(zm.zm_upload_disk_bytes(hv) // 4 + 4, device=dev)
+    zm.zm_upload_disk(hv, dbuf)
+    big = torch.from_numpy(synth.blob_image(4000, 4000, 24, workload=SYNTH_WORKLOAD_ID, index=6000)).to(dev)
+    cout = torch.empty((1, 1, 2), device=dev)
+    work = torch.empty(zm.zm_cartesian_work_bytes(1, 1) // 8 + 1, dtype=torch.float64, device=dev)
+    zm.zm_cartesian_moments([big], [(100, 36)], cout, work)
+    specs = synth.uneven_batch_specs(count=64, workload=3)
+    items = []
+    for j, (size, n_max, n_rho, n_theta) in enumerate(specs):
+        im = torch.from_numpy(synth.blob_image(size, size, 8, workload=3, index=j)).to(dev)
+        items.append((im, n_max, n_rho, n_theta, torch.empty((zm.zm_num_moments(n_max), 2), device=dev)))
+    b = zm.zm_batch_create(items, zm.ZM_PREC_FP16X3)
+    zm.zm_batch_run(b, items)
+    torch.cuda.synchronize(dev)
+    zm.zm_batch_destroy(b)
+    srv = zm.zm_server_create(1 << 30, 2, 8, zm.ZM_PREC_BF16X3)
+    keep = []
+    for j, (sz, nm) in enumerate([(256, 20), (512, 50), (1024, 100), (256, 20)]):
+        im = synth.blob_image(sz, sz, 8, workload=5, index=j)
+        o = np.empty((zm.zm_num_moments(nm), 2), np.float32)
+        nt = 1
+        while nt < 2 * nm + 2:
+            nt *= 2
+        keep.append((im, o))
+        zm.zm_server_submit(srv, im, nm, sz // 2, nt, o)
+    zm.zm_server_drain(srv)
+    zm.zm_server_destroy(srv)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_pass": "done", "launches": zm.zm_launch_count()}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_pass:
+        profile_pass()
     else:
         run_gb300(args)
 
