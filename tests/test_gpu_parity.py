@@ -426,6 +426,45 @@ def test_4k_bench_configuration_sampled():
             assert metrics.rel_max_err(Z[b], oracle_moments(img, p)) <= TOL_Z
 
 
+def test_4k_bench_step_bf16x3_sampled():
+    """The step bench.py times, in its launch configuration: 16 4K frames, bf16x3
+    plan, zm_resample -> zm_moments_polar -> zm_reconstruct_errors (Neumann).
+    Frames 0 and 15: moments against the oracle, the reconstruction of the
+    GPU's moments on sampled rings against the oracle's Eq. 9, and Eq. 10 /
+    Eq. 13 against sums over the GPU's own polar samples and reconstruction."""
+    B, n_max, n_rho, n_theta = 16, 100, 1024, 1024
+    imgs = [synth.blob_image(2160, 3840, 32, workload=2, index=b) for b in (0, 15)]
+    others = [torch.rand((2160, 3840), device=DEV) for _ in range(B - 2)]
+    with Plan(n_max, n_rho, n_theta, zm.ZM_PREC_BF16X3) as p:
+        ts = [dev(imgs[0])] + others + [dev(imgs[1])]
+        fhat = torch.empty((B, n_rho, n_theta), device=DEV)
+        out = torch.empty((B, p.P, 2), device=DEV)
+        frec = torch.empty((B, n_rho, n_theta), device=DEV)
+        err = torch.empty((B, 4), device=DEV, dtype=torch.float64)
+        zm.zm_resample(p.h, ts, fhat)
+        zm.zm_moments_polar(p.h, fhat, B, out, 0)
+        zm.zm_reconstruct_errors(p.h, out, B, frec, fhat, err, zm.ZM_NEUMANN)
+        torch.cuda.synchronize()
+        Z = as_complex(out)
+        e = err.cpu().numpy()
+        rings = np.array([0, 1, 7, 8, 255, 512, 1000, 1023])
+        rho, _ = grid.radial_nodes(n_rho)
+        k = np.arange(n_theta)[None, :]
+        m = np.arange(n_max + 1)[:, None]
+        basis = np.cos(2 * np.pi * ((m * k) % n_theta) / n_theta) + 1j * np.sin(2 * np.pi * ((m * k) % n_theta) / n_theta)
+        for b, img in ((0, imgs[0]), (B - 1, imgs[1])):
+            assert metrics.rel_max_err(Z[b], oracle_moments(img, p)) <= TOL_Z, b
+            rec_ref = (orc.radial_spectrum(Z[b], n_max, rho[rings], neumann=True) @ basis).real
+            got = frec[b, rings].double().cpu().numpy()
+            assert np.max(np.abs(got - rec_ref)) <= 1e-4 * np.max(np.abs(rec_ref)), b
+            f = fhat[b].double().cpu().numpy()
+            r = frec[b].double().cpu().numpy()
+            sd = np.sum((f - r) ** 2)
+            assert abs(e[b, 0] - sd / np.sum(f * f)) <= 1e-4 * e[b, 0], b
+            assert abs(e[b, 1] - sd / (f.max() ** 2 * f.size)) <= 1e-4 * e[b, 1], b
+            assert e[b, 3] == n_rho * n_theta
+
+
 # ------------------------------------------------------------------ host frames -> disk boxes
 @pytest.mark.parametrize("pinned", [True, False])
 def test_upload_disk_boxes_give_the_same_moments(pinned):
