@@ -73,21 +73,23 @@ def test_no_gpu_plan_fails_cleanly(zm):
     assert e.value.status == zm.ZM_ECUDA
 
 
-def test_upload_traffic_lies_between_the_stencils_and_the_box(zm):
+@pytest.mark.parametrize("geo", [None, (150.5, 100.0, 80.0), (30.0, 40.5, 70.0)])
+def test_upload_traffic_lies_between_the_stencils_and_the_box(zm, geo):
     """zm_upload_disk_traffic (host logic, no GPU): at least the bytes of the
     columns the bilinear stencils of the oracle's polar samples touch in each
     row (from the 4-aligned first column), at most that plus the spans' margins,
-    and less than the bounding box."""
+    and less than the bounding box; centred, off-centre and edge-clipped disks."""
     import numpy as np
     from oracle import grid
     h, w, n_rho, n_theta = 270, 480, 135, 512
     img = np.zeros((h, w), np.float32)
     host = [img]
-    traffic = zm.zm_upload_disk_traffic(host)
-    box = zm.zm_upload_disk_bytes(host)
+    geos = [geo] if geo else None
+    traffic = zm.zm_upload_disk_traffic(host, geometries=geos)
+    box = zm.zm_upload_disk_bytes(host, geometries=geos)
     rho, _ = grid.radial_nodes(n_rho)
     theta = 2 * np.pi * np.arange(n_theta) / n_theta
-    X, Y = grid.polar_to_pixel(rho[:, None], theta[None, :], grid.default_geometry(h, w))
+    X, Y = grid.polar_to_pixel(rho[:, None], theta[None, :], geo if geo else grid.default_geometry(h, w))
     x0, y0 = np.floor(X).astype(int).ravel(), np.floor(Y).astype(int).ravel()
     lo, hi = {}, {}
     for dy in (0, 1):
