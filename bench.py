@@ -16,6 +16,14 @@ the timed region, and reported as plan_ms.
 Several GPUs run independent replicas (no collective); the value is the images
 of all ranks divided by the slowest rank's time.  ``--impl reference`` times
 the FP64 CPU oracle instead, on bounded ring samples of the same workload.
+
+Without ``--quick`` the line also carries: the same step on two concurrent
+pipelines, moments-only rates per precision, one-frame latency, end to end
+from pinned host frames, an uneven batch in one graph launch, Poisson serving,
+reconstruction error vs order up to 500 (Gauss-Legendre and midpoint nodes),
+a colour frame, the Cartesian-summation route (Eq. 3-6) at 1000-4000 pixels,
+and the oracle timed on the host cores.  ``--profile-pass`` runs every kernel
+path once, for a profiler's launch list, and measures nothing.
 """
 
 import argparse
