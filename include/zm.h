@@ -146,6 +146,14 @@ int zm_plan_nodes(zm_plan_t plan, double* rho, double* wr, void* stream);
  *  imgs  host array of `batch` device image descriptors (any sizes)
  *  out   device float[batch][P][2]
  *  flags ZM_NEUMANN divides each moment by eps_m (2 for m = 0, else 1; Eq. 14)
+ * Path: images with a 16-byte aligned base and a pitch and width that are
+ * multiples of 4 floats are resampled and ring-transformed in one kernel (the
+ * polar samples stay on chip) when a plan has at most 2^17 polar samples per
+ * image, where that kernel measured faster; larger grids resample by image
+ * tiles into a workspace first.  Both paths give the same moments, bit for
+ * bit.  The environment variable ZM_FUSED, read when a plan is created,
+ * overrides the choice: "1" fuses wherever the geometry fits the kernel's
+ * stage buffers, "0" never fuses.
  * Errors: ZM_EINVAL (batch < 1, null pointers, image < 1x1, bad pitch),
  * ZM_ENOMEM (workspace growth), ZM_ECUDA.
  */

@@ -578,28 +578,42 @@ static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int 
     return ZM_OK;
 }
 
-// Ring spectra of a batch.  Polar input: FFT only.  Images: runs of
-// TMA-eligible images of one geometry go through the tile resampler into the
+// Ring spectra of a batch.  Polar input: FFT only.  Images: runs of one
+// geometry that the fused kernel can stage go through it when the plan's
+// fused_mode allows (resampling and ring FFT in one pass, polar samples
+// written only to the caller's fhat_out);
+// other runs of TMA-eligible images go through the tile resampler into the
 // polar buffer (the caller's fhat_out, else the plan workspace) and then the
-// ring FFT; runs of other images take the fused gather kernel.
+// ring FFT; the rest take the gather kernel.
 int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* F,
                    float* fhat_out, bool resample_only, cudaStream_t st, uint8_t* Fblk) {
     if (fhat_in) return launch_polar_fft(p, fhat_in, 0, batch, batch, F, Fblk, st);
+    const bool fuse = p->fused_mode > 0 ||
+                      (p->fused_mode == 0 && (long long)p->n_rho * p->n_theta <= FUSED_AUTO_SAMPLES);
+    auto use_fused = [&](int b) { return fuse && !resample_only && !p->tune_gather && fused_eligible(p, imgs[b]); };
     auto use_tma = [&](int b) { return !p->tune_gather && tma_eligible(imgs[b]); };
-    bool any_tma = false;
-    for (int b = 0; b < batch && !any_tma; ++b) any_tma = use_tma(b);
     float* fh = fhat_out;
-    if (any_tma && !fh) {
-        const int s = p->ws_fhat.grow(sizeof(float) * (size_t)batch * p->n_rho * p->n_theta);
-        if (s != ZM_OK) return s;
-        fh = (float*)p->ws_fhat.ptr;
-    }
     int b = 0;
     while (b < batch) {
         int e = b + 1;
         int s;
+        if (use_fused(b)) {
+            while (e < batch && use_fused(e) && same_geometry(imgs[b], imgs[e])) ++e;
+            s = launch_ring_fused(p, imgs, b, e - b, batch, F, Fblk, fhat_out, st);
+            if (s == ZM_OK) {
+                b = e;
+                continue;
+            }
+            if (s != ZM_EUNSUPPORTED) return s;
+            e = b + 1;                       // a geometry the stage buffers cannot hold
+        }
         if (use_tma(b)) {
             while (e < batch && use_tma(e) && same_geometry(imgs[b], imgs[e])) ++e;
+            if (!fh) {
+                s = p->ws_fhat.grow(sizeof(float) * (size_t)batch * p->n_rho * p->n_theta);
+                if (s != ZM_OK) return s;
+                fh = (float*)p->ws_fhat.ptr;
+            }
             s = launch_resample_tiles(p, imgs, b, e - b, fh, st);
             if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, Fblk, st);
         } else {

@@ -200,6 +200,11 @@ struct zm_plan_s {
     int tune_gather = 0;        // 1: resample with the fused gather kernel even where TMA could stage
     int tune_rings = 0;         // rings per CTA of the ring-FFT kernels (2, 4 or 8)
     int tune_split = 0;         // CTAs per SM aimed at by the projection's radial split
+    // resampling fused with the ring FFT (ring_fused.cu): 0 = for images of at
+    // most FUSED_AUTO_SAMPLES polar samples (where it measured faster than
+    // the tile resampler + ring FFT), 1 = wherever it applies, -1 = never;
+    // set from the environment variable ZM_FUSED ("1" / "0") at plan creation
+    int fused_mode = 0;
 };
 
 namespace zm {
@@ -288,5 +293,13 @@ bool tma_eligible(const zm_image_t& im);
 bool same_geometry(const zm_image_t& a, const zm_image_t& b);
 int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st);
 void release_tiles(zm_plan_t p);
+
+// Resampling fused with the ring FFT (ring_fused.cu): polar samples stay on chip
+constexpr long long FUSED_AUTO_SAMPLES = 1ll << 17;
+bool fused_eligible(zm_plan_t p, const zm_image_t& im);
+int launch_ring_fused(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int batch, float* F, uint8_t* Fblk,
+                      float* fhat_out, cudaStream_t st);
+long long fused_staged_bytes(zm_plan_t p, const zm_image_t& im);
+void release_fused(zm_plan_t p);
 
 }  // namespace zm
