@@ -252,7 +252,8 @@ int zm_project(zm_plan_t plan, const float* spectra, int batch, float* out,
  *    ZM_EINVAL without touching the device.
  *  - The first call on a device looks up the array's device address (set-up,
  *    with that device current); make that first call before any stream
- *    capture.
+ *    capture.  The address is kept for the process's lifetime: resetting the
+ *    device (cudaDeviceReset) between calls is not supported.
  *  - All calls on a device share the array and it keeps the last call's
  *    contents; each call overwrites the part it reads, so nothing needs
  *    clearing, but calls that overlap on the GPU (other streams, other

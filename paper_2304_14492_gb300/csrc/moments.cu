@@ -489,19 +489,41 @@ __global__ void k_project_reduce(const float* __restrict__ part, int S, int P, i
     out[(size_t)idx * 2 + 1] = im * f;
 }
 
-static int launch_projection_fp32(zm_plan_t p, const float* F, int batch, float* out, unsigned flags,
-                                  cudaStream_t st) {
-    const int ncol = 2 * batch;
-    const int ctiles = (ncol + KC_COLS - 1) / KC_COLS;
+// Radial split of the FP32 projection: S slices of `chunk` nodes (a multiple
+// of KC_K) aiming at the tuned number of CTAs per SM, at most max_slices of
+// them (re-deriving S from the chunk never raises it).
+static void fp32_split(zm_plan_t p, int batch, long long max_slices, int* S_out, int* chunk_out) {
+    const int ctiles = (2 * batch + KC_COLS - 1) / KC_COLS;
     const int base = (p->n_max + 1) * ctiles;
     const int target = (p->tune_split > 0 ? p->tune_split : 4) * num_sms(p->device);
     const int kchunks = (p->n_rho + KC_K - 1) / KC_K;
-    int S = std::max(1, std::min(kchunks, (target + base - 1) / base));
-    const int chunk = ((kchunks + S - 1) / S) * KC_K;
-    S = (p->n_rho + chunk - 1) / chunk;
-    int st_ = p->ws_part.grow(sizeof(float) * (size_t)S * p->P * ncol);
+    long long S = std::max(1, std::min(kchunks, (target + base - 1) / base));
+    S = std::max(1ll, std::min(S, max_slices));
+    const int chunk = (int)((kchunks + S - 1) / S) * KC_K;
+    *S_out = (p->n_rho + chunk - 1) / chunk;
+    *chunk_out = chunk;
+}
+
+static int launch_projection_fp32(zm_plan_t p, const float* F, int batch, float* out, unsigned flags,
+                                  cudaStream_t st) {
+    int S, chunk;
+    fp32_split(p, batch, 1ll << 40, &S, &chunk);
+    const int st_ = p->ws_part.grow(sizeof(float) * (size_t)S * p->P * 2 * batch);
     if (st_ != ZM_OK) return st_;
-    float* part = (float*)p->ws_part.ptr;
+    return launch_projection_fp32_parts(p, F, batch, out, flags, (float*)p->ws_part.ptr,
+                                        p->ws_part.bytes / sizeof(float), st);
+}
+
+int launch_projection_fp32_parts(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, float* part,
+                                 size_t part_floats, cudaStream_t st) {
+    const int ncol = 2 * batch;
+    const size_t one_slice = (size_t)p->P * ncol;
+    if (one_slice > part_floats)
+        return set_error(ZM_EINVAL, "projection partial sums: %zu floats per slice, %zu available", one_slice,
+                         part_floats);
+    int S, chunk;
+    fp32_split(p, batch, (long long)(part_floats / one_slice), &S, &chunk);
+    const int ctiles = (ncol + KC_COLS - 1) / KC_COLS;
     dim3 grid(p->n_max + 1, ctiles, S);
     k_project_fp32<<<grid, 256, 0, st>>>(p->A32, F, p->mrow, p->n_max, p->n_rho, ncol,
                                           chunk, p->P, part);

@@ -215,6 +215,10 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
                    float* F, float* fhat_out, bool resample_only, cudaStream_t st, uint8_t* Fblk = nullptr);
 int launch_projection(zm_plan_t p, const float* F, int batch, float* out, unsigned flags,
                       cudaStream_t st);
+// FP32 split-K projection with its partial sums in `part` (part_floats floats);
+// the radial split is lowered until its slices fit (ZM_EINVAL if one does not).
+int launch_projection_fp32_parts(zm_plan_t p, const float* F, int batch, float* out, unsigned flags, float* part,
+                                 size_t part_floats, cudaStream_t st);
 // Moments of a batch (images, or polar samples when fhat_in is set): ring
 // spectra, then the projection; bf16 plans take the blocked tensor-core path.
 int launch_moments(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* out,
