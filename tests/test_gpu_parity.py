@@ -427,11 +427,13 @@ def test_4k_bench_configuration_sampled():
 
 
 def test_4k_bench_step_bf16x3_sampled():
-    """The step bench.py times, in its launch configuration: 16 4K frames, bf16x3
-    plan, zm_resample -> zm_moments_polar -> zm_reconstruct_errors (Neumann).
-    Frames 0 and 15: moments against the oracle, the reconstruction of the
-    GPU's moments on sampled rings against the oracle's Eq. 9, and Eq. 10 /
-    Eq. 13 against sums over the GPU's own polar samples and reconstruction."""
+    """The step bench.py times, in its launch configuration: zm_moments on 16 4K
+    frames with a bf16x3 plan; frames 0 and 15 against the oracle at the split
+    form's bar (2e-5 max|Z|).  Then the reconstruction step the bench times
+    beside it: zm_moments_ex (polar samples kept) -> zm_reconstruct_errors
+    (Neumann), with the reconstruction of the GPU's moments on sampled rings
+    against the oracle's Eq. 9, and Eq. 10 / Eq. 13 against sums over the GPU's
+    own polar samples and reconstruction."""
     B, n_max, n_rho, n_theta = 16, 100, 1024, 1024
     imgs = [synth.blob_image(2160, 3840, 32, workload=2, index=b) for b in (0, 15)]
     others = [torch.rand((2160, 3840), device=DEV) for _ in range(B - 2)]
@@ -441,11 +443,16 @@ def test_4k_bench_step_bf16x3_sampled():
         out = torch.empty((B, p.P, 2), device=DEV)
         frec = torch.empty((B, n_rho, n_theta), device=DEV)
         err = torch.empty((B, 4), device=DEV, dtype=torch.float64)
-        zm.zm_resample(p.h, ts, fhat)
-        zm.zm_moments_polar(p.h, fhat, B, out, 0)
+        zm.zm_moments(p.h, ts, out, 0)
+        torch.cuda.synchronize()
+        Zm = as_complex(out)
+        for b, img in ((0, imgs[0]), (B - 1, imgs[1])):
+            assert metrics.rel_max_err(Zm[b], oracle_moments(img, p)) <= 2e-5, b
+        zm.zm_moments_ex(p.h, ts, out, fhat, 0)
         zm.zm_reconstruct_errors(p.h, out, B, frec, fhat, err, zm.ZM_NEUMANN)
         torch.cuda.synchronize()
         Z = as_complex(out)
+        assert np.array_equal(Z, Zm)
         e = err.cpu().numpy()
         rings = np.array([0, 1, 7, 8, 255, 512, 1000, 1023])
         rho, _ = grid.radial_nodes(n_rho)

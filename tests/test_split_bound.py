@@ -1,0 +1,64 @@
+"""The error bound of the split-precision projection, checked in CPU arithmetic.
+
+The tensor-core projection of Eq. 1 computes each product a*f of a weight
+a = (n+1)/pi * w_i * 2pi/N_theta * R_nm(rho_i) and a spectrum value f as
+a_hi f_hi + a_hi f_lo + a_lo f_hi, where x_hi is x rounded to the 16-bit format
+(p significant bits: 8 for bf16, 11 for fp16) and x_lo is x - x_hi rounded
+again.  With u = 2^-p:
+
+    |x - x_hi - x_lo| <= u^2 |x|,      |x_lo| <= u |x|,
+
+so one product is off by at most |a_lo f_lo| + |a_hi||f - f_hi - f_lo| +
+|a - a_hi - a_lo||f_hi| <= 3 u^2 |a f| (to first order), and the moment
+
+    |Z_split - Z| <= 3 u^2 S_nm,   S_nm = sum_i |a_i| |f_i|
+
+(3 * 2^-16 * 2^-2 = 3 * 2^-18 for bf16, 3 * 2^-22 for fp16), before the FP32
+rounding of the accumulation.  The products here are emulated exactly (float64
+holds every product of two 16-bit values and their short sums), so the test
+sees the split alone: the bf16 and fp16 splits stay inside the bound on the
+64x64 and 512x512 workloads, and splits that keep less (a shorter lo part, a
+dropped cross term, no lo part) break it, so the bound detects them.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2304_14492_gb300 import synth
+from splitmath import rne, split_moments, terms
+
+
+WORKLOADS = {
+    "64x64 uniform, n_max 20": (lambda: synth.uniform_image(64, 64, workload=0, index=0), (20, 32, 64)),
+    "512x512 blobs, n_max 50": (lambda: synth.blob_image(512, 512, 8, workload=1, index=0), (50, 256, 256)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(WORKLOADS))
+def workload(request):
+    make, args = WORKLOADS[request.param]
+    return terms(make(), *args)
+
+
+def test_rounding_helper_matches_known_values():
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7 at 8 bits: to even -> 1
+    assert rne(np.array([1.0 + 2.0 ** -8]), 8)[0] == 1.0
+    assert rne(np.array([1.0 + 3 * 2.0 ** -8]), 8)[0] == 1.0 + 2.0 ** -6
+    assert rne(np.array([np.pi]), 11)[0] == np.float64(np.float16(np.pi))
+    x = np.linspace(-3, 3, 1001)
+    assert np.array_equal(rne(x, 11), x.astype(np.float16).astype(np.float64))
+
+
+@pytest.mark.parametrize("p", [8, 11])
+def test_split_stays_inside_its_bound(workload, p):
+    a, f, z, S = workload
+    err = np.abs(split_moments(a, f, p) - z)
+    bound = 3 * 2.0 ** (-2 * p - 2) * S
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("weaker", [dict(lo_bits=4), dict(terms_kept=("hh", "hl")), dict(terms_kept=("hh",))])
+def test_weaker_bf16_splits_break_the_bound(workload, weaker):
+    a, f, z, S = workload
+    err = np.abs(split_moments(a, f, 8, **weaker) - z)
+    assert np.max(err / (3 * 2.0 ** -18 * S)) > 1.0
