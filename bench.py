@@ -4,29 +4,35 @@
 Workload: 3840x2160 float32 frames of 32 random anisotropic Gaussian blobs
 (centres area-uniform in the disk, sigma 5-40 px, amplitude 0.2-1) plus noise
 of standard deviation 0.01, the disk of diameter 2160 centred; moments up to
-n_max = 100 on a 1024 x 1024 polar grid.  A step is one pass of the whole hot
-path over a batch of B frames already resident in HBM:
-  bilinear polar resampling (Sec. 2.5, polar samples kept) -> ring real FFT
-  and radial projection (Eq. 1) -> reconstruction on the polar nodes (Eq. 9,
-  Neumann) with the reconstruction errors on the polar nodes (Eq. 10, Eq. 13)
-  accumulated in the same kernel.
-The FP64 radial-polynomial table (Eq. 7) is built once at plan time, outside
-the timed region, and reported as plan_ms.
+n_max = 100 on a 1024 x 1024 polar grid.  A step is one zm_moments call on a
+batch of B frames already resident in HBM: bilinear polar resampling
+(Sec. 2.5), the real FFT of every ring and the radial projection of Eq. 1 with
+the bf16 hi + lo split on the tensor cores.  The FP64 radial-polynomial table
+(Eq. 7) is built once at plan time, outside the timed region (plan_ms).
+
+The line carries the step time's median and p99 over 200 steps with warm and
+with flushed L2, and one roofline per stage, each timed over its own loop of
+100 launches: K-b (resampling + ring FFT: zm_stage_spectra), K-c (projection:
+zm_stage_project), K-d (reconstruction on the polar nodes: zm_reconstruct);
+algorithmic bytes count only what the method must move (the image sectors the
+stencils touch, the spectra, tables and results), never an intermediate.
 
 Several GPUs run independent replicas (no collective); the value is the images
 of all ranks divided by the slowest rank's time.  ``--impl reference`` times
 the FP64 CPU oracle instead, on bounded ring samples of the same workload.
 
-Without ``--quick`` the line also carries: the same step on two concurrent
-pipelines, moments-only rates per precision, one-frame latency, end to end
-from pinned host frames, an uneven batch in one graph launch, Poisson serving,
-reconstruction error vs order up to 500 (Gauss-Legendre and midpoint nodes),
-a colour frame, the Cartesian-summation route (Eq. 3-6) at 1000-4000 pixels,
-and the oracle timed on the host cores.  ``--profile-pass`` runs every kernel
-path once, for a profiler's launch list, and measures nothing.
+Without ``--quick`` the line also carries: the FP32 and fp16x3 forms' rates
+and every form's error against the FP64 oracle, the reconstruction step,
+one-frame latency, end to end from pinned host frames, two concurrent
+pipelines, an uneven batch in one graph launch, serving swept over arrival
+rates with per-request errors against the oracle, reconstruction error vs
+order up to 500, a colour frame, the Cartesian-summation route (Eq. 3-6) and
+the oracle timed on the host cores.  ``--profile-pass`` runs every kernel path
+once, for a profiler's launch list, and measures nothing.
 """
 
 import argparse
+import functools
 import json
 import os
 import statistics
@@ -150,44 +156,40 @@ def make_frames(n, start=0):
     return [synth.blob_image(H, W, N_BLOBS, workload=SYNTH_WORKLOAD_ID, index=start + b) for b in range(n)]
 
 
-def read_profile_traffic(kernel_tag):
-    """Per-launch DRAM bytes of `kernel_tag` from the committed ncu summary, if
-    the summary was taken on the current kernel source."""
+def read_profile_traffic(name):
+    """Per-image DRAM bytes of a stage from the committed ncu summary
+    profiles/<name>.md, if the summary was taken on the current sources of the
+    kernels it names (a line "source_sha: <file> <sha12> ..." per file)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", kernel_tag + "_4k.md")
-    src = os.path.join(ROOT, "paper_2304_14492_gb300", "csrc", "resample_tiles.cu")
-    if not (os.path.exists(path) and os.path.exists(src)):
-        return None, None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
-    traffic, src_sha, batch = None, None, None
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None, "no ncu summary"
+    traffic, shas = None, []
     for line in open(path):
         if line.startswith("traffic_bytes_per_image:"):
             traffic = float(line.split(":")[1].split()[0])
         if line.startswith("source_sha:"):
-            src_sha = line.split(":")[1].strip()
-    if src_sha != sha:
-        return None, "kernel changed since the ncu capture"
+            parts = line.split(":", 1)[1].split()
+            shas += list(zip(parts[0::2], parts[1::2]))
+    for fname, sha in shas:
+        src = os.path.join(ROOT, "paper_2304_14492_gb300", "csrc", fname)
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:12] != sha:
+            return None, "%s changed since the ncu capture" % fname
     return traffic, None
 
 
 # ---------------------------------------------------------------- oracle timing
 def oracle_pass(img, ring_idx):
-    """The FP64 oracle on the rings `ring_idx` of one frame: resampling, angular
-    DFT, partial radial projection, reconstruction on those rings, errors."""
+    """The FP64 oracle's moments restricted to the rings `ring_idx` of one
+    frame: bilinear resampling, angular DFT and the partial radial projection
+    (the whole step's work scales with the rings)."""
     import oracle
     rho_all, wr_all = oracle.grid.radial_nodes(N_RHO)
     rho, wr = rho_all[ring_idx], wr_all[ring_idx]
     fhat = oracle.resample.polar_resample(img, rho, N_THETA, geometry())
     F = oracle.moments.angular_dft(fhat, N_MAX)
     table = oracle.zernike.zrp_table(N_MAX, rho)
-    Z = oracle.moments.project(F, wr, N_THETA, N_MAX, table=table)
-    G = oracle.reconstruct.radial_spectrum(Z, N_MAX, rho, neumann=True)
-    k = np.arange(N_THETA)[None, :]
-    m = np.arange(N_MAX + 1)[:, None]
-    ang = 2 * np.pi * ((m * k) % N_THETA) / N_THETA
-    rec = (G @ (np.cos(ang) + 1j * np.sin(ang))).real
-    d = fhat - rec
-    return Z, float(np.sum(d * d) / np.sum(fhat * fhat))
+    return oracle.moments.project(F, wr, N_THETA, N_MAX, table=table)
 
 
 def blas_threads():
@@ -210,7 +212,7 @@ def cpu_baseline(img, budget_s=12.0):
     n = 0
     Zref = None
     while True:
-        Z, _ = oracle_pass(img, rings)
+        Z = oracle_pass(img, rings)
         if Zref is None:
             Zref = Z
         n += 1
@@ -218,7 +220,8 @@ def cpu_baseline(img, budget_s=12.0):
         if el >= budget_s or n >= 64:
             break
     return {"value": n / el, "unit": "images/s", "cores": blas_threads(), "kind": "oracle",
-            "sample": "%d whole 4K frame(s) through the FP64 oracle (moments + polar reconstruction + errors), "
+            "sample": "%d whole 4K frame(s) through the FP64 oracle (moments: resampling, angular DFT, "
+                      "projection), "
                       "%.1f s of CPU time, numpy/BLAS on %d host cores" % (n, el, os.cpu_count())}, Zref
 
 
@@ -256,6 +259,123 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def event_loop(torch, st, fn, reps):
+    """Mean device time (ms) of `fn` over `reps` back-to-back calls on stream st."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def step_distribution(torch, dev, st, step, steps=200):
+    """Per-step device time (events around each step), warm L2 and with L2
+    flushed (a 256 MB write) before every step: median and p99 in ms."""
+    flush = torch.empty(64 * 2**20, device=dev, dtype=torch.float32)
+    out = {}
+    for name, cold in (("warm_l2", False), ("cold_l2", True)):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            if cold:
+                flush.fill_(float(k))
+            ev[k][0].record(st)
+            step()
+            ev[k][1].record(st)
+        torch.cuda.synchronize(dev)
+        t = sorted(a.elapsed_time(b) for a, b in ev)
+        out[name] = {"median_ms": statistics.median(t), "p99_ms": t[min(steps - 1, int(0.99 * steps))],
+                     "steps": steps}
+    del flush
+    return out
+
+
+def stage_rooflines(zm, torch, dev, st, plan, descs, B, P, hbm, peaks, reps=100):
+    """One roofline per stage of the step, each over its own loop of `reps`
+    launches: K-b = zm_stage_spectra (resampling + ring FFT), K-c =
+    zm_stage_project (radial projection), K-d = zm_reconstruct (radial
+    reconstruction + inverse ring FFT on the polar nodes, Neumann).
+    Algorithmic bytes per image: K-b the distinct 32-byte image sectors the
+    bilinear stencils touch plus the spectra written; K-c the split table
+    once per batch, the spectra and the moments; K-d the split table once per
+    batch, the moments and the polar reconstruction written."""
+    sectors = touched_sector_bytes()
+    f_bytes = (N_MAX + 1) * N_RHO * 8                      # F_m(rho_i), complex64 (bf16 hi + lo: same bytes)
+    table = 2 * 2 * P * N_RHO                              # hi + lo bf16 halves
+    z_bytes = P * 8
+    polar = N_RHO * N_THETA * 4
+    out = torch.empty((B, P, 2), device=dev)
+    frec = torch.empty((B, N_RHO, N_THETA), device=dev)
+    zm.zm_stage_spectra(plan, descs, st)
+    zm.zm_stage_project(plan, B, out, 0, st)
+    l0 = zm.zm_launch_count()
+    zm.zm_stage_spectra(plan, descs, st)
+    kb_launches = zm.zm_launch_count() - l0
+    torch.cuda.synchronize(dev)
+    res = {}
+    t = event_loop(torch, st, lambda: zm.zm_stage_spectra(plan, descs, st), reps)
+    kb = B * (sectors + f_bytes)
+    res["K-b"] = {"bound": "hbm", "launch_ms": t, "algorithmic_bytes_per_launch": kb,
+                  "achieved": kb / (t / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s", "frac": kb / (t / 1000.0) / 1e9 / hbm,
+                  "kernels_per_call": kb_launches,
+                  "path": "fused resampling + ring FFT" if kb_launches == 1 else "tile resampler, then ring FFT",
+                  "per_image_bytes": {"touched_sectors": sectors, "spectra_out": f_bytes, "disk_box": disk_box_bytes()}}
+    zm.zm_stage_spectra(plan, descs, st)
+    t = event_loop(torch, st, lambda: zm.zm_stage_project(plan, B, out, 0, st), reps)
+    kc = table + B * (f_bytes + z_bytes)
+    flops = 4.0 * P * N_RHO * B
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    res["K-c"] = {"bound": "hbm", "launch_ms": t, "algorithmic_bytes_per_launch": kc,
+                  "achieved": kc / (t / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": kc / (t / 1000.0) / 1e9 / hbm, "algorithmic_tflops": flops / (t / 1000.0) / 1e12,
+                  "executed_tflops": 3 * flops / (t / 1000.0) / 1e12, "bf16_peak_tflops": bf16,
+                  "tensor_frac_executed": 3 * flops / (t / 1000.0) / 1e12 / bf16,
+                  "note": "B=%d is below the bf16 ridge (%.0f flop/B), so the table and spectra traffic bounds it"
+                          % (B, bf16 * 1e12 / (hbm * 1e9))}
+    t = event_loop(torch, st, lambda: zm.zm_reconstruct(plan, out, B, frec, zm.ZM_NEUMANN, st), reps)
+    kd = table + B * (z_bytes + polar)
+    res["K-d"] = {"bound": "hbm", "launch_ms": t, "algorithmic_bytes_per_launch": kd,
+                  "achieved": kd / (t / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": kd / (t / 1000.0) / 1e9 / hbm, "algorithmic_tflops": flops / (t / 1000.0) / 1e12}
+    # the fused kernel on the same frames (a plan made with ZM_FUSED=1), for
+    # its DRAM traffic and time beside the tile path
+    old = os.environ.get("ZM_FUSED")
+    os.environ["ZM_FUSED"] = "1"
+    try:
+        pf = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
+    finally:
+        if old is None:
+            del os.environ["ZM_FUSED"]
+        else:
+            os.environ["ZM_FUSED"] = old
+    try:
+        zm.zm_plan_reserve(pf, B)
+        zm.zm_stage_spectra(pf, descs, st)
+        t = event_loop(torch, st, lambda: zm.zm_stage_spectra(pf, descs, st), reps)
+        res["K-b_fused"] = {"launch_ms": t, "achieved": kb / (t / 1000.0) / 1e9, "frac": kb / (t / 1000.0) / 1e9 / hbm,
+                            "note": "the fused resampling + ring FFT kernel forced on this grid (ZM_FUSED=1); "
+                                    "zm_moments fuses up to 2^17 polar samples per image"}
+    finally:
+        zm.zm_plan_destroy(pf)
+    for key, name in (("K-b", "kb_tile_4k_b16" if kb_launches > 1 else "kb_fused_4k_b16"),
+                      ("K-b_fused", "kb_fused_4k_b16")):
+        traffic, note = read_profile_traffic(name)
+        res[key]["traffic"] = traffic * B if traffic else None
+        if note:
+            res[key]["traffic_note"] = note
+        elif traffic:
+            res[key]["traffic_over_algorithmic"] = traffic / (sectors + f_bytes)
+    return res
+
+
 def run_gb300(args):
     import torch
 
@@ -289,34 +409,14 @@ def run_gb300(args):
         prec = "fp32"
         plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, pflag[prec])
     plan_ms = 1000 * (time.perf_counter() - t0)
-    plan32 = plan if prec == "fp32" else zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_FP32)
     zm.zm_plan_reserve(plan, B)
-    zm.zm_plan_reserve(plan32, B)
 
     st = torch.cuda.current_stream(dev)
     out = torch.empty((B, P, 2), device=dev)
-    fhat = torch.empty((B, N_RHO, N_THETA), device=dev)
-    frec = torch.empty((B, N_RHO, N_THETA), device=dev)
-    err = torch.empty((B, 4), device=dev, dtype=torch.float64)
-
     descs = zm.image_array(views)            # the frames' descriptors, built once like a caller would
 
-    def step(ev=None, segments=True):
-        # resampling (tile kernel) | ring FFT + projection | reconstruction | errors.
-        # An event between two kernels stops the next one from launching early
-        # (programmatic dependent launch) and costs the step several us, so the
-        # timed loop brackets the resampler on every SAMPLE-th step only
-        if ev is not None:
-            ev[0].record(st)
-        zm.zm_resample(plan, descs, fhat, st)
-        if ev is not None:
-            ev[1].record(st)
-        zm.zm_moments_polar(plan, fhat, B, out, 0, st)
-        if ev is not None and segments:
-            ev[2].record(st)
-        zm.zm_reconstruct_errors(plan, out, B, frec, fhat, err, zm.ZM_NEUMANN, st)
-        if ev is not None and segments:
-            ev[3].record(st)
+    def step():
+        zm.zm_moments(plan, descs, out, 0, st)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -331,72 +431,57 @@ def run_gb300(args):
         gpu_id = str(local)
     sampler = ClockSampler(gpu_id)
     sampler.start()
-    SAMPLE = 8
-    kb = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(0, args.steps, SAMPLE)]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     l0 = zm.zm_launch_count()
     ev0.record(st)
-    for k in range(args.steps):
-        step(kb[k // SAMPLE] if k % SAMPLE == 0 else None, segments=False)
+    for _ in range(args.steps):
+        step()
     ev1.record(st)
     torch.cuda.synchronize(dev)
     l1 = zm.zm_launch_count()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms, dev)
-    kb_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in kb)
     value = job_throughput(world, B, args.steps, ms)
-    # segment breakdown from a separate, instrumented pass (events between the
-    # three calls; slower than the timed loop for the reason above)
-    nseg = min(args.steps, 50)
-    sg = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nseg)]
-    for k in range(nseg):
-        step(sg[k])
-    torch.cuda.synchronize(dev)
-    seg = [statistics.mean(e[j].elapsed_time(e[j + 1]) for e in sg) for j in range(3)]
 
-    # roofline of the dominant kernel (tile resampler): algorithmic bytes per
-    # launch = touched image sectors + polar samples written, per frame
-    sectors = touched_sector_bytes()
-    f_bytes = (N_MAX + 1) * N_RHO * 8
-    fhat_bytes = N_RHO * N_THETA * 4
-    kb_bytes = B * (sectors + fhat_bytes)
-    import json as _json
-    peaks = {}
-    try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = kb_bytes / (kb_ms / 1000.0) / 1e9
-    traffic, traffic_note = read_profile_traffic("k_resample_tiles")
-    roofline = {"bound": "hbm", "kernel": "k_resample_tiles", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": (traffic * B if traffic else None),
-                "algorithmic_bytes_per_launch": kb_bytes, "launch_ms": kb_ms,
-                "launch_timing": "CUDA events around the resampler on every %d-th step of the timed loop" % SAMPLE,
+    dist_t = step_distribution(torch, dev, st, step)
+    stages = stage_rooflines(zm, torch, dev, st, plan, descs, B, P, hbm, peaks)
+    kb = stages["K-b"]
+    roofline = {"bound": "hbm", "stage": "K-b (resampling + ring FFT)", "path": kb["path"],
+                "achieved": kb["achieved"], "peak": hbm, "unit": "GB/s", "frac": kb["achieved"] / hbm,
+                "traffic": kb.get("traffic"), "algorithmic_bytes_per_launch": kb["algorithmic_bytes_per_launch"],
+                "launch_ms": kb["launch_ms"],
+                "launch_timing": "CUDA events around 100 back-to-back zm_stage_spectra calls (the stage alone)",
                 "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback",
-                "per_image_bytes": {"touched_sectors": sectors, "polar_samples_out": fhat_bytes,
-                                    "disk_box": disk_box_bytes()},
-                "step_segments_ms": {"resample": seg[0], "ring_fft+projection": seg[1],
-                                     "reconstruction+errors": seg[2],
-                                     "note": "separate pass of %d steps with events between the calls" % nseg}}
-    if traffic_note:
-        roofline["traffic_note"] = traffic_note
-
+                "per_image_bytes": kb["per_image_bytes"]}
+    if "traffic_note" in kb:
+        roofline["traffic_note"] = kb["traffic_note"]
+    sectors = kb["per_image_bytes"]["touched_sectors"]
+    f_bytes = kb["per_image_bytes"]["spectra_out"]
+    step_ms = ms / args.steps
     line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == "fp32" else prec.replace("x3", "x3+f32acc"), "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "global_batch": B * world,
                        "precision": prec, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (%d MB of frames per step)" % (B * H * W * 4 // 2**20),
-                       "step": "resampling + ring FFT + projection + polar reconstruction (Neumann) + polar errors"},
-            "roofline": roofline, "gpu_launches": l1 - l0, "clocks": clocks, "plan_ms": plan_ms}
+                       "step": "zm_moments: resampling + ring FFT + radial projection (bf16 hi+lo split, "
+                               "FP32 accumulate)"},
+            "step_time": dist_t,
+            "whole_step_hbm": {"algorithmic_bytes_per_image": sectors + 2 * f_bytes,
+                               "achieved_gbs": B * (sectors + 2 * f_bytes) / (step_ms / 1000.0) / 1e9,
+                               "frac": B * (sectors + 2 * f_bytes) / (step_ms / 1000.0) / 1e9 / hbm,
+                               "note": "touched sectors + spectra written and read back, per image, over the "
+                                       "whole step time (the split table, 10.65 MB per batch, stays in L2)"},
+            "roofline": roofline, "stages": stages, "gpu_launches": l1 - l0, "clocks": clocks, "plan_ms": plan_ms}
 
     if rank == 0 and not args.quick:
+        line.update(extras(args, zm, torch, dev, st, plan, prec, views, descs, out, B, P))
         line["pipelined"] = bench_pipelined(zm, torch, dev, descs, B, P)
-        line.update(extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P))
         line["colour"] = bench_colour(zm, torch, dev, plan, P)
         del views, imgs
         torch.cuda.empty_cache()
@@ -407,43 +492,62 @@ def run_gb300(args):
         line["serving"] = bench_serving(zm)
         line["cpu_baseline"], Zref = cpu_baseline(img0)
         line["err_vs_fp64"] = {k: float(np.max(np.abs(z - Zref)) / np.max(np.abs(Zref))) for k, z in frame0.items()}
+        line["err_bars"] = {"fp32": 1e-4, "bf16x3": 2e-5, "fp16x3": 2e-5,
+                            "note": "max|Z - Z_fp64| / max|Z_fp64| per frame; the split forms' per-moment bound "
+                                    "3 u^2 sum_i |a_i f_i| is asserted in the tests"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
-    if plan32 != plan:
-        zm.zm_plan_destroy(plan32)
     zm.zm_plan_destroy(plan)
 
 
-def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
+def extras(args, zm, torch, dev, st, plan, prec, views, descs, out, B, P):
     res = {}
-    # moments-only throughput, mixed precision vs FP32 on the same frames
-    def moments_rate(p, reps=50):
-        for _ in range(5):
-            zm.zm_moments(p, views, out, 0, st)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(reps):
-            zm.zm_moments(p, views, out, 0, st)
-        e1.record(st)
-        torch.cuda.synchronize(dev)
-        return B * reps / (e0.elapsed_time(e1) / 1000.0)
+    pflag = {"fp32": zm.ZM_PREC_FP32, "bf16x3": zm.ZM_PREC_BF16X3, "fp16x3": zm.ZM_PREC_FP16X3}
+    plans = {prec: plan}
+    for name in ("fp32", "bf16x3", "fp16x3"):
+        if name not in plans:
+            plans[name] = zm.zm_plan(N_MAX, N_RHO, N_THETA, pflag[name])
+            zm.zm_plan_reserve(plans[name], B)
 
-    res["moments_only_images_per_s"] = {prec: moments_rate(plan)}
-    if plan32 != plan:
-        res["moments_only_images_per_s"]["fp32"] = moments_rate(plan32)
+    # moments per precision on the same frames: the mixed forms against FP32
+    rates = {}
+    for name, p in plans.items():
+        for _ in range(5):
+            zm.zm_moments(p, descs, out, 0, st)
+        t = event_loop(torch, st, lambda: zm.zm_moments(p, descs, out, 0, st), 100)
+        rates[name] = B / (t / 1000.0)
+    res["moments_images_per_s"] = rates
+    res["mixed_over_fp32"] = {k: v / rates["fp32"] for k, v in rates.items() if k != "fp32"}
 
     # frame 0 through every precision; compared with the FP64 oracle's moments
     # of the same frame, which the cpu_baseline leg computes while it is timed
     frame0 = {}
-    for name, p in ((prec, plan), ("fp32", plan32)):
+    for name, p in plans.items():
         o1 = torch.empty((1, P, 2), device=dev)
         zm.zm_moments(p, [views[0]], o1, 0, st)
         torch.cuda.synchronize(dev)
         z = o1[0].double().cpu().numpy()
         frame0[name] = z[:, 0] + 1j * z[:, 1]
     res["_frame0"] = (views[0].double().cpu().numpy(), frame0)
+
+    # the reconstruction step beside the moments: moments with the polar
+    # samples kept, Neumann reconstruction on the polar nodes, Eq. 10 / Eq. 13
+    fh = torch.empty((B, N_RHO, N_THETA), device=dev)
+    fr = torch.empty((B, N_RHO, N_THETA), device=dev)
+    er = torch.empty((B, 4), device=dev, dtype=torch.float64)
+
+    def rec_step():
+        zm.zm_moments_ex(plan, descs, out, fh, 0, st)
+        zm.zm_reconstruct_errors(plan, out, B, fr, fh, er, zm.ZM_NEUMANN, st)
+
+    for _ in range(3):
+        rec_step()
+    t = event_loop(torch, st, rec_step, 50)
+    res["reconstruction_step"] = {"ms_per_batch": t, "images_per_s": B / (t / 1000.0),
+                                  "step": "zm_moments_ex + zm_reconstruct_errors (Neumann, polar nodes)"}
+    del fh, fr, er
 
     # single-frame latency (L2 flushed between calls)
     flush = torch.empty(64 * 2**20, device=dev, dtype=torch.float32)     # 256 MB > L2
@@ -464,21 +568,17 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
     del flush
 
     # end to end through the public API: pinned host frames -> disk spans on
-    # the device (zm_upload_disk, a kernel reading the pinned frames) -> full
-    # step -> moments and errors back to the host.  Two device buffers: the
-    # upload of step k + 1 runs on its own stream while step k computes (the
-    # host link, not the GPU, bounds this path)
+    # the device (zm_upload_disk, a kernel reading the pinned frames) ->
+    # zm_moments -> moments back to the host.  Two device buffers: the upload
+    # of step k + 1 runs on its own stream while step k computes (the host
+    # link, not the GPU, bounds this path)
     host = torch.empty((B, H, W), dtype=torch.float32, pin_memory=True)
     host.copy_(torch.stack([v for v in views]).cpu())
     hviews = [host[b] for b in range(B)]
     box_bytes = zm.zm_upload_disk_bytes(hviews)
     h2d_bytes = zm.zm_upload_disk_traffic(hviews)
     dbufs = [torch.empty(box_bytes // 4 + 4, device=dev) for _ in range(2)]
-    fh = torch.empty((B, N_RHO, N_THETA), device=dev)
-    fr = torch.empty((B, N_RHO, N_THETA), device=dev)
-    er = torch.empty((B, 4), device=dev, dtype=torch.float64)
     hout = torch.empty((B, P, 2), dtype=torch.float32, pin_memory=True)
-    herr = torch.empty((B, 4), dtype=torch.float64, pin_memory=True)
     s_up = torch.cuda.Stream(dev)
     up_done = [torch.cuda.Event() for _ in range(2)]
     read_done = [torch.cuda.Event() for _ in range(2)]
@@ -493,11 +593,9 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
     def compute(k):
         j = k % 2
         st.wait_event(up_done[j])
-        zm.zm_moments_ex(plan, boxes[j], out, fh, 0, st)
+        zm.zm_moments(plan, boxes[j], out, 0, st)
         read_done[j].record(st)
-        zm.zm_reconstruct_errors(plan, out, B, fr, fh, er, zm.ZM_NEUMANN, st)
         hout.copy_(out, non_blocking=True)
-        herr.copy_(er, non_blocking=True)
 
     def run(n):
         upload(0)
@@ -516,33 +614,29 @@ def extras(args, zm, torch, dev, st, plan, plan32, prec, views, out, B, P):
     e1.record(st)
     torch.cuda.synchronize(dev)
     res["e2e"] = {"value": B * reps / (e0.elapsed_time(e1) / 1000.0), "unit": "images/s",
-                  "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": B * P * 8 + B * 4 * 8,
+                  "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": B * P * 8,
                   "steps": reps,
                   "h2d": "row spans of the disks of the pinned frames, read by a kernel (zm_upload_disk), "
                          "the next step's upload overlapping this step's compute"}
+    for name, p in plans.items():
+        if p != plan:
+            zm.zm_plan_destroy(p)
     return res
 
 
 def bench_pipelined(zm, torch, dev, descs, B, P, pipelines=2, batches=200):
-    """The same step on `pipelines` independent pipelines (plan, buffers and
-    stream each), batches dealt round-robin: the memory-bound resampler of one
-    batch overlaps the issue-bound ring FFTs of another.  Whole-job frames/s;
-    the headline stays the one-stream step, whose kernel timings the roofline
-    needs."""
+    """The headline step on `pipelines` independent pipelines (plan, buffers
+    and stream each), batches dealt round-robin: the memory-bound resampler of
+    one batch overlaps the issue-bound ring FFT and projection of another.
+    Whole-job frames/s; the headline stays the one-stream step."""
     pipes = []
     for _ in range(pipelines):
         plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
         zm.zm_plan_reserve(plan, B)
-        pipes.append({"plan": plan, "st": torch.cuda.Stream(dev),
-                      "fhat": torch.empty((B, N_RHO, N_THETA), device=dev),
-                      "out": torch.empty((B, P, 2), device=dev),
-                      "frec": torch.empty((B, N_RHO, N_THETA), device=dev),
-                      "err": torch.empty((B, 4), device=dev, dtype=torch.float64)})
+        pipes.append({"plan": plan, "st": torch.cuda.Stream(dev), "out": torch.empty((B, P, 2), device=dev)})
 
     def step(q):
-        zm.zm_resample(q["plan"], descs, q["fhat"], q["st"])
-        zm.zm_moments_polar(q["plan"], q["fhat"], B, q["out"], 0, q["st"])
-        zm.zm_reconstruct_errors(q["plan"], q["out"], B, q["frec"], q["fhat"], q["err"], zm.ZM_NEUMANN, q["st"])
+        zm.zm_moments(q["plan"], descs, q["out"], 0, q["st"])
 
     for k in range(4 * pipelines):
         step(pipes[k % pipelines])
@@ -565,8 +659,8 @@ def bench_pipelined(zm, torch, dev, descs, B, P, pipelines=2, batches=200):
         zm.zm_plan_destroy(q["plan"])
     return {"pipelines": pipelines, "batches": batches, "batch": B, "ms_per_batch": ms / batches,
             "images_per_s": B * batches / (ms / 1000.0),
-            "note": "the step of the headline on %d streams at once (a plan and buffers each), batches "
-                    "dealt round-robin" % pipelines}
+            "note": "zm_moments on %d streams at once (a plan and buffers each), batches dealt round-robin"
+                    % pipelines}
 
 
 def bench_stability(zm, torch, dev):
@@ -726,75 +820,135 @@ def bench_uneven(zm, torch, dev, count=256):
     return res
 
 
-def bench_serving(zm, rate=2000.0, seconds=10.0, seed=7):
+SERVE_SIZES, SERVE_ORDERS = (256, 512, 1024, 2160), (20, 50, 100, 200)
+
+
+@functools.lru_cache(maxsize=16)
+def serve_image(size, k):
+    """Image k of a serving size class: blob frames, 2160 = the centred
+    2160x2160 crop of a 3840x2160 frame."""
+    from paper_2304_14492_gb300 import synth
+    if size == 2160:
+        f = synth.blob_image(H, W, N_BLOBS, workload=5, index=k)
+        return np.ascontiguousarray(f[:, (W - H) // 2:(W - H) // 2 + H])
+    return synth.blob_image(size, size, 8, workload=5, index=k)
+
+
+def serve_n_theta(n_max):
+    nt = 1
+    while nt < 2 * n_max + 2:
+        nt *= 2
+    return nt
+
+
+def _oracle_request(args):
+    """Worker: the FP64 oracle's moments of one served request (image rebuilt
+    from its seed) and the relative max error of the served result."""
+    size, k, n_max, got = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    img = serve_image(size, k).astype(np.float64)
+    ref = oracle.moments.moments(img, n_max, size // 2, serve_n_theta(n_max))
+    z = got[:, 0].astype(np.float64) + 1j * got[:, 1].astype(np.float64)
+    return size, n_max, float(np.max(np.abs(z - ref)) / np.max(np.abs(ref)))
+
+
+def bench_serving(zm, rates=(2000.0, 8000.0, 32000.0, 128000.0), max_requests=20000, seconds=10.0, seed=7,
+                  per_cell=16):
     """Poisson arrivals of host images (sizes 256/512/1024/2160-crop, n_max
     20/50/100/200, N_rho = size/2, N_theta = next power of two >= 2 n_max + 2)
-    into the continuous-batching server; latency submit -> result on the host."""
-    from paper_2304_14492_gb300 import synth
+    into the continuous-batching server, swept from 2000 requests/s past
+    saturation; latency submit -> result on the host.  At the highest rate,
+    `per_cell` requests of every (size, n_max) cell are checked against the
+    FP64 oracle (process pool on the host cores), and every request of that
+    run is run again alone and compared with its result in the mix."""
+    import multiprocessing as mp
     rng = np.random.default_rng(seed)
-    sizes, orders = [256, 512, 1024, 2160], [20, 50, 100, 200]
-    pool = {}
-    for sz in sizes:
-        if sz == 2160:
-            frames = [synth.blob_image(H, W, N_BLOBS, workload=5, index=k) for k in range(2)]
-            pool[sz] = [np.ascontiguousarray(f[:, (W - H) // 2:(W - H) // 2 + H]) for f in frames]
-        else:
-            pool[sz] = [synth.blob_image(sz, sz, 8, workload=5, index=k) for k in range(4)]
-    n = int(rate * seconds)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
-    reqs = []
-    for j in range(n):
-        sz = int(rng.choice(sizes))
-        nm = int(rng.choice(orders))
-        nt = 1
-        while nt < 2 * nm + 2:
-            nt *= 2
-        img = pool[sz][j % len(pool[sz])]
-        reqs.append((img, nm, sz // 2, nt, np.empty((zm.zm_num_moments(nm), 2), np.float32)))
+    pool = {sz: [serve_image(sz, k) for k in range(2 if sz == 2160 else 4)] for sz in SERVE_SIZES}
     srv = zm.zm_server_create(4 << 30, 4, 64, zm.ZM_PREC_BF16X3)
+    sweep, last = [], None
     try:
         # resident plans for every grid first (plan builds are not request latency)
-        warm = [(sz, nm, np.empty((zm.zm_num_moments(nm), 2), np.float32)) for sz in sizes for nm in orders]
+        warm = [(sz, nm, np.empty((zm.zm_num_moments(nm), 2), np.float32)) for sz in SERVE_SIZES
+                for nm in SERVE_ORDERS]
         for sz, nm, o in warm:                 # the outputs stay referenced until drained
-            zm.zm_server_submit(srv, pool[sz][0], nm, sz // 2, 1 << max(3, (2 * nm + 1).bit_length()), o)
+            zm.zm_server_submit(srv, pool[sz][0], nm, sz // 2, serve_n_theta(nm), o)
         zm.zm_server_drain(srv, 120.0)
-        zm.zm_server_reset_stats(srv)
-        t0 = time.perf_counter()
-        for (img, nm, nr, nt, out), ta in zip(reqs, arrivals):
-            while time.perf_counter() - t0 < ta:
-                pass
-            zm.zm_server_submit(srv, img, nm, nr, nt, out)
-        zm.zm_server_drain(srv, 120.0)
-        wall = time.perf_counter() - t0
-        stats = zm.zm_server_stats(srv)
-        # every request again, alone (submit, wait), against its result in the mix
+        for rate in rates:
+            n = int(min(max_requests, rate * seconds))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+            reqs = []
+            for j in range(n):
+                sz = int(rng.choice(SERVE_SIZES))
+                nm = int(rng.choice(SERVE_ORDERS))
+                k = j % len(pool[sz])
+                reqs.append((sz, k, nm, np.empty((zm.zm_num_moments(nm), 2), np.float32)))
+            zm.zm_server_reset_stats(srv)
+            t0 = time.perf_counter()
+            late = 0.0
+            for (sz, k, nm, out), ta in zip(reqs, arrivals):
+                now = time.perf_counter() - t0
+                while now < ta:
+                    now = time.perf_counter() - t0
+                late = max(late, now - ta)
+                zm.zm_server_submit(srv, pool[sz][k], nm, sz // 2, serve_n_theta(nm), out)
+            zm.zm_server_drain(srv, 120.0)
+            wall = time.perf_counter() - t0
+            stats = zm.zm_server_stats(srv)
+            done = int(stats["completed"])
+            sweep.append({"arrival_rate_per_s": rate, "requests": n, "completed": done,
+                          "offered_s": float(arrivals[-1]), "wall_s": wall, "images_per_s": done / wall,
+                          "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "max_ms": stats["max_ms"],
+                          "groups_launched": int(stats["groups_launched"]),
+                          "requests_per_group": done / max(1, int(stats["groups_launched"])),
+                          "peak_device_bytes": int(stats["peak_bytes"]),
+                          "submit_lag_max_ms": 1000.0 * late})
+            last = reqs
+        # every request of the highest-rate run again, alone, against its result in the mix
         worst, rerun, t1 = 0.0, 0, time.perf_counter()
-        for img, nm, nr, nt, out in reqs:
+        for sz, k, nm, out in last:
             if time.perf_counter() - t1 > 60.0:
                 break
             o = np.empty_like(out)
-            zm.zm_server_wait(srv, zm.zm_server_submit(srv, img, nm, nr, nt, o), 30.0)
-            d = float(np.max(np.abs(o - out)) / max(float(np.max(np.abs(o))), 1e-30))
-            worst = max(worst, d)
+            zm.zm_server_wait(srv, zm.zm_server_submit(srv, pool[sz][k], nm, sz // 2, serve_n_theta(nm), o), 30.0)
+            worst = max(worst, float(np.max(np.abs(o - out)) / max(float(np.max(np.abs(o))), 1e-30)))
             rerun += 1
+        host_direct = bool(zm.zm_server_stats(srv)["host_direct"])
     finally:
         zm.zm_server_destroy(srv, 60.0)
     del warm
-    done = stats["completed"]
-    return {"arrival_rate_per_s": rate, "requests": n, "completed": int(done), "wall_s": wall,
-            "images_per_s": done / wall, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
-            "max_ms": stats["max_ms"], "groups_launched": int(stats["groups_launched"]),
-            "peak_device_bytes": int(stats["peak_bytes"]), "precision": "bf16x3",
+    # per-request error against the FP64 oracle: the first `per_cell` requests
+    # of every (size, n_max) cell of the highest-rate run
+    picked, seen = [], {}
+    for sz, k, nm, out in last:
+        if seen.get((sz, nm), 0) < per_cell:
+            seen[(sz, nm)] = seen.get((sz, nm), 0) + 1
+            picked.append((sz, k, nm, out))
+    t2 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pp:
+        errs = pp.map(_oracle_request, picked, chunksize=1)
+    cells = {}
+    for sz, nm, e in errs:
+        c = cells.setdefault("%dx%d n_max=%d" % (sz, sz, nm), {"requests": 0, "max_rel_err": 0.0})
+        c["requests"] += 1
+        c["max_rel_err"] = max(c["max_rel_err"], e)
+    return {"precision": "bf16x3", "host_direct": host_direct, "sweep": sweep,
             "alone_vs_mix": {"requests_rerun": rerun, "max_rel_diff": worst},
-            "host_direct": bool(stats["host_direct"]),
-            "note": "statistics reset after 16 plan-warming requests; latency = submit -> moments in host memory"}
+            "err_vs_fp64": {"cells": cells, "worst": max(c["max_rel_err"] for c in cells.values()),
+                            "bar": 2e-5, "oracle_s": time.perf_counter() - t2,
+                            "note": "max|Z - Z_fp64| / max|Z_fp64| per request, %d requests per (size, n_max) "
+                                    "cell of the %.0f/s run" % (per_cell, rates[-1])},
+            "note": "statistics reset per rate after 16 plan-warming requests; latency = submit -> moments in "
+                    "host memory; submit_lag = how late the Python submitter was against the Poisson schedule"}
 
 
 def profile_pass():
     """Every kernel path of the library once, at the bench's sizes where it has
-    one: plan builds, the FP32 and FP16 projection forms on 16 4K frames, the
-    fused gather path (frames TMA cannot stage), the FP32 reconstruction with
-    errors, pixel reconstruction and normalisation (a colour frame), the upload
+    one: plan builds, the FP32 and FP16 projection forms on 16 4K frames (the
+    stage calls and the tile path), the fused resampling + ring FFT kernel on
+    the same frames, the gather path (frames TMA cannot stage), the FP32
+    reconstruction with errors, pixel reconstruction and normalisation (a
+    colour frame), the upload
     of host frames, the Cartesian route at 4000 x 4000, an uneven batch and a
     few served requests.  For a launch-list capture under a profiler: prints
     one line and measures nothing."""
@@ -815,6 +969,8 @@ def profile_pass():
     for prec in (zm.ZM_PREC_FP32, zm.ZM_PREC_FP16X3, zm.ZM_PREC_BF16X3):
         plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, prec)
         zm.zm_plan_reserve(plan, B)
+        zm.zm_stage_spectra(plan, views)
+        zm.zm_stage_project(plan, B, out)
         zm.zm_moments_ex(plan, views, out, fh)
         zm.zm_reconstruct_errors(plan, out, B, fr, fh, err, zm.ZM_NEUMANN)
         if prec == zm.ZM_PREC_FP32:
@@ -826,6 +982,13 @@ def profile_pass():
             zm.zm_project(plan, spectra, 4, out[:4])
         torch.cuda.synchronize(dev)
         zm.zm_plan_destroy(plan)
+    os.environ["ZM_FUSED"] = "1"                 # the fused kernel on the 4K grid as well
+    for prec in (zm.ZM_PREC_FP32, zm.ZM_PREC_BF16X3):
+        plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, prec)
+        zm.zm_moments(plan, views, out)
+        torch.cuda.synchronize(dev)
+        zm.zm_plan_destroy(plan)
+    del os.environ["ZM_FUSED"]
     plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
     bench_colour(zm, torch, dev, plan, P, steps=1)
     zm.zm_plan_destroy(plan)

@@ -262,6 +262,20 @@ int zm_project(zm_plan_t plan, const float* spectra, int batch, float* out,
 int zm_project_noalloc(zm_plan_t plan, const float* spectra, int batch, float* out,
                        unsigned flags, void* stream);
 
+/* The two stages of zm_moments as separate calls (Eq. 1): zm_stage_spectra
+ * computes the ring spectra F_m(rho_i), m <= n_max, of `batch` images (the
+ * resampling and angular FFT of zm_moments) into the plan's workspace, in the
+ * form the plan's projection reads; zm_stage_project then applies the radial
+ * projection (and ZM_NEUMANN) to them and writes out = device
+ * float[batch][P][2].  zm_moments gives the same moments as the two calls in
+ * turn.  Use them to time or overlap the stages; the spectra stay in the plan
+ * until the next call that computes spectra with this plan, so calls on one
+ * plan must not overlap on the GPU.  zm_stage_project returns ZM_EINVAL if
+ * `batch` differs from the last zm_stage_spectra's.  Asynchronous on
+ * `stream`; zm_stage_spectra may grow the workspace (cudaMalloc). */
+int zm_stage_spectra(zm_plan_t plan, const zm_image_t* imgs, int batch, void* stream);
+int zm_stage_project(zm_plan_t plan, int batch, float* out, unsigned flags, void* stream);
+
 /* ---- uneven batches ------------------------------------------------------ */
 
 /* One request of an uneven batch: an image with its own order and polar grid.

@@ -653,24 +653,33 @@ int launch_projection(zm_plan_t p, const float* F, int batch, float* out, unsign
     return launch_projection_tc(p, F, batch, out, flags, st);
 }
 
+// Stage 1 of the moments: ring spectra of a batch (images, or polar samples
+// when fhat_in is set) into the plan's workspace, in the form its projection
+// reads (bf16 operand blocks for the blocked tensor-core projection, FP32
+// rows otherwise).
+int launch_stage_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* fhat_out,
+                         cudaStream_t st) {
+    if (blocked_projection(p)) {
+        const size_t half = fblk_half_bytes(p->n_max, p->n_chunks, 2 * batch);
+        const int s = p->ws_Fblk.grow(2 * half);
+        if (s != ZM_OK) return s;
+        return launch_spectra(p, imgs, fhat_in, batch, nullptr, fhat_out, false, st, (uint8_t*)p->ws_Fblk.ptr);
+    }
+    const int s = p->ws_F.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
+    if (s != ZM_OK) return s;
+    return launch_spectra(p, imgs, fhat_in, batch, (float*)p->ws_F.ptr, fhat_out, false, st);
+}
+
+// Stage 2: the radial projection of the spectra stage 1 left in the workspace.
+int launch_stage_project(zm_plan_t p, int batch, float* out, unsigned flags, cudaStream_t st) {
+    if (blocked_projection(p)) return launch_projection_blocked(p, (const uint8_t*)p->ws_Fblk.ptr, batch, out, flags, st);
+    return launch_projection(p, (const float*)p->ws_F.ptr, batch, out, flags, st);
+}
+
 int launch_moments(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* out,
                    float* fhat_out, unsigned flags, cudaStream_t st) {
-    if (blocked_projection(p)) {
-        // spectra straight into bf16 operand blocks, then the blocked projection
-        const size_t half = fblk_half_bytes(p->n_max, p->n_chunks, 2 * batch);
-        int s = p->ws_Fblk.grow(2 * half);
-        if (s != ZM_OK) return s;
-        uint8_t* Fb = (uint8_t*)p->ws_Fblk.ptr;
-        s = launch_spectra(p, imgs, fhat_in, batch, nullptr, fhat_out, false, st, Fb);
-        if (s != ZM_OK) return s;
-        return launch_projection_blocked(p, Fb, batch, out, flags, st);
-    }
-    int s = p->ws_F.grow(sizeof(float) * (size_t)(p->n_max + 1) * batch * 2 * p->n_rho);
-    if (s != ZM_OK) return s;
-    float* F = (float*)p->ws_F.ptr;
-    s = launch_spectra(p, imgs, fhat_in, batch, F, fhat_out, false, st);
-    if (s != ZM_OK) return s;
-    return launch_projection(p, F, batch, out, flags, st);
+    const int s = launch_stage_spectra(p, imgs, fhat_in, batch, fhat_out, st);
+    return s != ZM_OK ? s : launch_stage_project(p, batch, out, flags, st);
 }
 
 }  // namespace zm
@@ -734,6 +743,28 @@ extern "C" int zm_project(zm_plan_t plan, const float* spectra, int batch, float
     if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
     DeviceGuard g(plan->device);
     return launch_projection(plan, spectra, batch, out, flags, (cudaStream_t)stream);
+}
+
+extern "C" int zm_stage_spectra(zm_plan_t plan, const zm_image_t* imgs, int batch, void* stream) {
+    if (!plan) return set_error(ZM_EINVAL, "plan is NULL");
+    const int s = check_images(imgs, batch);
+    if (s != ZM_OK) return s;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return set_error(ZM_ECUDA, "cannot select device %d", plan->device);
+    const int r = launch_stage_spectra(plan, imgs, nullptr, batch, nullptr, (cudaStream_t)stream);
+    plan->staged_batch = (r == ZM_OK) ? batch : 0;
+    return r;
+}
+
+extern "C" int zm_stage_project(zm_plan_t plan, int batch, float* out, unsigned flags, void* stream) {
+    if (!plan || !out) return set_error(ZM_EINVAL, "NULL argument");
+    if (flags & ~ZM_NEUMANN) return set_error(ZM_EINVAL, "unknown flags 0x%x", flags);
+    if (batch < 1 || batch != plan->staged_batch)
+        return set_error(ZM_EINVAL, "zm_stage_project: batch %d, but the plan holds spectra of %d images", batch,
+                         plan->staged_batch);
+    DeviceGuard g(plan->device);
+    if (!g.ok) return set_error(ZM_ECUDA, "cannot select device %d", plan->device);
+    return launch_stage_project(plan, batch, out, flags, (cudaStream_t)stream);
 }
 
 extern "C" int zm_plan_reserve(zm_plan_t plan, int batch) {

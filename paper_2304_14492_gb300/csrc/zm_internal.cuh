@@ -205,6 +205,7 @@ struct zm_plan_s {
     // the tile resampler + ring FFT), 1 = wherever it applies, -1 = never;
     // set from the environment variable ZM_FUSED ("1" / "0") at plan creation
     int fused_mode = 0;
+    int staged_batch = 0;       // images whose spectra zm_stage_spectra left in the workspace
 };
 
 namespace zm {

@@ -87,6 +87,8 @@ SIGNATURES = {
     "zm_ring_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p, c_void_p, c_void_p]),
     "zm_project": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_project_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_uint, c_void_p]),
+    "zm_stage_spectra": (c_int, [c_void_p, POINTER(zm_image_t), c_int, c_void_p]),
+    "zm_stage_project": (c_int, [c_void_p, c_int, c_void_p, c_uint, c_void_p]),
     "zm_batch_create": (c_int, [POINTER(c_void_p), POINTER(zm_request_t), c_int, c_uint]),
     "zm_batch_run": (c_int, [c_void_p, POINTER(zm_request_t), c_uint, c_void_p]),
     "zm_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
@@ -349,6 +351,15 @@ def zm_ring_spectra(plan, images, spectra, fhat=None, stream=None, geometries=No
 
 def zm_project(plan, spectra, batch, out, flags=0, stream=None):
     _check(lib().zm_project(plan, _ptr(spectra), batch, _ptr(out), flags, _stream(stream)))
+
+
+def zm_stage_spectra(plan, images, stream=None, geometries=None):
+    arr, n = _images(images, geometries)
+    _check(lib().zm_stage_spectra(plan, arr, n, _stream(stream)))
+
+
+def zm_stage_project(plan, batch, out, flags=0, stream=None):
+    _check(lib().zm_stage_project(plan, batch, _ptr(out), flags, _stream(stream)))
 
 
 def zm_project_noalloc(plan, spectra, batch, out, flags=0, stream=None):

@@ -685,3 +685,23 @@ def test_ring_spectra_cross_check_against_cufft(n_max, n_rho, n_theta):
     got = torch.complex(F[:, 0, 0, :].double(), F[:, 0, 1, :].double()).T     # [i][m]
     err = (got - ref).abs().max().item()
     assert err <= 2e-6 * ref.abs().max().item() * np.log2(n_theta), err
+
+
+# ------------------------------------------------------------------ the two stages of zm_moments
+@pytest.mark.parametrize("prec", [zm.ZM_PREC_FP32, zm.ZM_PREC_BF16X3, zm.ZM_PREC_FP16X3])
+def test_stage_calls_equal_zm_moments(prec):
+    imgs = [synth.blob_image(256, 320, 8, workload=26, index=b) for b in range(3)]
+    ts = [dev(i) for i in imgs]
+    with Plan(40, 100, 128, prec) as p:
+        a = torch.empty((3, p.P, 2), device=DEV)
+        b = torch.empty((3, p.P, 2), device=DEV)
+        zm.zm_moments(p.h, ts, a, zm.ZM_NEUMANN)
+        zm.zm_stage_spectra(p.h, ts)
+        zm.zm_stage_project(p.h, 3, b, zm.ZM_NEUMANN)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        with pytest.raises(zm.ZmError) as e:
+            zm.zm_stage_project(p.h, 2, b)
+        assert e.value.status == zm.ZM_EINVAL
+    ref = oracle_moments(imgs[1], p, neumann=True)
+    assert metrics.rel_max_err(as_complex(a)[1], ref) <= TOL_Z
