@@ -942,7 +942,7 @@ def bench_serving(zm, rates=(2000.0, 8000.0, 32000.0, 128000.0), max_requests=20
                     "host memory; submit_lag = how late the Python submitter was against the Poisson schedule"}
 
 
-def profile_pass():
+def profile_pass(batch=16):
     """Every kernel path of the library once, at the bench's sizes where it has
     one: plan builds, the FP32 and FP16 projection forms on 16 4K frames (the
     stage calls and the tile path), the fused resampling + ring FFT kernel on
@@ -958,7 +958,7 @@ def profile_pass():
     from paper_2304_14492_gb300 import native as zm, synth
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    B = 16
+    B = batch
     imgs = torch.from_numpy(np.stack(make_frames(B))).to(dev)
     views = [imgs[b] for b in range(B)]
     P = zm.zm_num_moments(N_MAX)
@@ -1031,7 +1031,7 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.profile_pass:
-        profile_pass()
+        profile_pass(args.batch)
     else:
         run_gb300(args)
 
