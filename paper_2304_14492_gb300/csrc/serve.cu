@@ -201,13 +201,22 @@ static int launch_group(zm_server_t s, SrvGroup& g, cudaStream_t st) {
 }
 
 // Plan for a grid that covers order n_max (rebuilt only when n_max grows).
-static int grid_plan(zm_server_t s, int n_rho, int n_theta, int n_max, std::shared_ptr<GridPlan>* out) {
+// A build (table, weights, workspace; it ends in a device synchronisation)
+// runs with the server lock released, so submitters are not held up by it;
+// only this scheduler thread reads or changes the plan map.
+static int grid_plan(zm_server_t s, int n_rho, int n_theta, int n_max, std::shared_ptr<GridPlan>* out,
+                     std::unique_lock<std::mutex>& lk) {
     auto key = std::make_pair(n_rho, n_theta);
     auto it = s->plans.find(key);
     if (it != s->plans.end() && it->second->n_max >= n_max) {
         *out = it->second;
         return ZM_OK;
     }
+    lk.unlock();
+    struct Relock {
+        std::unique_lock<std::mutex>& l;
+        ~Relock() { l.lock(); }
+    } relock{lk};
     auto gp = std::make_shared<GridPlan>();
     int rc = zm_plan(&gp->plan, n_max, n_rho, n_theta, s->cfg.plan_flags);
     if (rc == ZM_OK) rc = zm_plan_reserve(gp->plan, s->cfg.max_group);
@@ -223,10 +232,11 @@ static int grid_plan(zm_server_t s, int n_rho, int n_theta, int n_max, std::shar
     return ZM_OK;
 }
 
-// One scheduler pass (called with s->mu held): retire finished groups, admit
-// waiting requests in arrival order while they fit, launch admitted requests
-// grouped by grid and flags.  Returns true if anything happened.
-static bool schedule_once(zm_server_t s) {
+// One scheduler pass (called with s->mu held through lk, which a plan build
+// releases for its duration): retire finished groups, admit waiting requests
+// in arrival order while they fit, launch admitted requests grouped by grid
+// and flags.  Returns true if anything happened.
+static bool schedule_once(zm_server_t s, std::unique_lock<std::mutex>& lk) {
     bool acted = false;
     // 1. completions (groups retire in any order)
     for (auto it = s->inflight.begin(); it != s->inflight.end();) {
@@ -295,7 +305,7 @@ static bool schedule_once(zm_server_t s) {
             g.reqs.push_back(s->admitted[j]);
             n_max = std::max(n_max, s->admitted[j].n_max);
         }
-        int rc = grid_plan(s, head.n_rho, head.n_theta, n_max, &g.gp);
+        int rc = grid_plan(s, head.n_rho, head.n_theta, n_max, &g.gp, lk);
         if (rc == ZM_OK) rc = launch_group(s, g, s->streams[sidx]);
         if (rc != ZM_OK) {
             s->error = rc;
@@ -325,7 +335,7 @@ static void scheduler(zm_server_t s) {
             s->waiting.clear();
             s->admitted.clear();
         }
-        const bool acted = schedule_once(s);
+        const bool acted = schedule_once(s, lk);
         const bool idle = s->incoming.empty() && s->waiting.empty() && s->admitted.empty() && s->inflight.empty();
         if (s->stop && idle) break;
         if (!acted) {
