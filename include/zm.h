@@ -153,7 +153,12 @@ int zm_plan_nodes(zm_plan_t plan, double* rho, double* wr, void* stream);
  * tiles into a workspace first.  Both paths give the same moments, bit for
  * bit.  The environment variable ZM_FUSED, read when a plan is created,
  * overrides the choice: "1" fuses wherever the geometry fits the kernel's
- * stage buffers, "0" never fuses.
+ * stage buffers, "0" never fuses.  ZM_RING_DFT=1, read likewise, sends bf16x3
+ * plans with n_max <= 127 to a third kernel that resamples and computes the
+ * angular sums of Eq. 1 as a product with the DFT matrix on the tensor cores
+ * (split operands, FP32 accumulation; moments within the split bar of the
+ * FFT paths, not bit-equal to them); it is off by default, being slower than
+ * the tile path on the 4K frame.
  * Errors: ZM_EINVAL (batch < 1, null pointers, image < 1x1, bad pitch),
  * ZM_ENOMEM (workspace growth), ZM_ECUDA.
  */

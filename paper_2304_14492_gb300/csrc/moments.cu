@@ -601,9 +601,11 @@ static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int 
 }
 
 // Ring spectra of a batch.  Polar input: FFT only.  Images: runs of one
-// geometry that the fused kernel can stage go through it when the plan's
-// fused_mode allows (resampling and ring FFT in one pass, polar samples
-// written only to the caller's fhat_out);
+// geometry go through the tensor-core DFT kernel when the plan asks for it
+// (dft_mode, off by default) and the spectra are wanted as operand blocks
+// only (no polar samples out), else through the fused kernel when its fused_mode allows (resampling
+// and ring FFT in one pass, polar samples written only to the caller's
+// fhat_out);
 // other runs of TMA-eligible images go through the tile resampler into the
 // polar buffer (the caller's fhat_out, else the plan workspace) and then the
 // ring FFT; the rest take the gather kernel.
@@ -612,6 +614,8 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
     if (fhat_in) return launch_polar_fft(p, fhat_in, 0, batch, batch, F, Fblk, st);
     const bool fuse = p->fused_mode > 0 ||
                       (p->fused_mode == 0 && (long long)p->n_rho * p->n_theta <= FUSED_AUTO_SAMPLES);
+    const bool dft = Fblk && !fhat_out && !resample_only && !p->tune_gather && p->dft_mode > 0;
+    auto use_dft = [&](int b) { return dft && dft_eligible(p, imgs[b]); };
     auto use_fused = [&](int b) { return fuse && !resample_only && !p->tune_gather && fused_eligible(p, imgs[b]); };
     auto use_tma = [&](int b) { return !p->tune_gather && tma_eligible(imgs[b]); };
     float* fh = fhat_out;
@@ -619,6 +623,16 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
     while (b < batch) {
         int e = b + 1;
         int s;
+        if (use_dft(b)) {
+            while (e < batch && use_dft(e) && same_geometry(imgs[b], imgs[e])) ++e;
+            s = launch_ring_dft(p, imgs, b, e - b, batch, Fblk, st);
+            if (s == ZM_OK) {
+                b = e;
+                continue;
+            }
+            if (s != ZM_EUNSUPPORTED) return s;
+            e = b + 1;                       // a geometry whose stages the buffers cannot hold
+        }
         if (use_fused(b)) {
             while (e < batch && use_fused(e) && same_geometry(imgs[b], imgs[e])) ++e;
             s = launch_ring_fused(p, imgs, b, e - b, batch, F, Fblk, fhat_out, st);

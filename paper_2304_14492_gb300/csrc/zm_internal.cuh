@@ -206,6 +206,12 @@ struct zm_plan_s {
     // set from the environment variable ZM_FUSED ("1" / "0") at plan creation
     int fused_mode = 0;
     int staged_batch = 0;       // images whose spectra zm_stage_spectra left in the workspace
+    // resampling with the angular transform on the tensor cores (ring_dft.cu),
+    // bf16 plans with the blocked projection: 1 = wherever it applies, else
+    // never (the default: the tile path measured faster on the 4K frame); set
+    // from the environment variable ZM_RING_DFT ("1") at plan creation
+    int dft_mode = 0;
+    uint8_t* dft = nullptr;     // its DFT tiles (bf16 hi / lo), built on first use
 };
 
 namespace zm {
@@ -306,5 +312,11 @@ int launch_ring_fused(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int b
                       float* fhat_out, cudaStream_t st);
 long long fused_staged_bytes(zm_plan_t p, const zm_image_t& im);
 void release_fused(zm_plan_t p);
+
+// Resampling fused with the angular transform as a tensor-core DFT
+// (ring_dft.cu): writes the blocked projection's operand blocks only
+bool dft_eligible(zm_plan_t p, const zm_image_t& im);
+int launch_ring_dft(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int batch, uint8_t* Fblk, cudaStream_t st);
+void release_dft(zm_plan_t p);
 
 }  // namespace zm

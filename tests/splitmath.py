@@ -46,3 +46,30 @@ def split_moments(a, f, p, lo_bits=None, terms_kept=("hh", "hl", "lh")):
     if "lh" in terms_kept:
         z += np.sum(al * fh, axis=1)
     return z
+
+
+def dft_matrix(n_max, n_theta):
+    """cos and -sin of 2 pi m k / N_theta for m = 0..n_max (the angular sums
+    of Eq. 1 as a matrix product), evaluated from m k mod N_theta in float64."""
+    idx = np.outer(np.arange(n_max + 1), np.arange(n_theta)) % n_theta
+    ang = 2 * np.pi * idx / n_theta
+    return np.cos(ang), -np.sin(ang)
+
+
+def dft_split_spectra(fh, n_max, p, lo_bits=None, terms_kept=("hh", "hl", "lh")):
+    """F_m(rho_i) = sum_k f_ik e^{-j m theta_k} from split samples and split
+    DFT entries (f_hi w_hi + f_hi w_lo + f_lo w_hi), exactly: [N_rho, n_max + 1]."""
+    c, s = dft_matrix(n_max, fh.shape[-1])
+    f_hi, f_lo = split(fh, p, lo_bits)
+    out = np.zeros((fh.shape[0], n_max + 1), dtype=np.complex128)
+    for part, sign in ((c, 1.0), (s, 1j)):
+        w_hi, w_lo = split(part, p, lo_bits)
+        acc = np.zeros((fh.shape[0], n_max + 1))
+        if "hh" in terms_kept:
+            acc += f_hi @ w_hi.T
+        if "hl" in terms_kept:
+            acc += f_hi @ w_lo.T
+        if "lh" in terms_kept:
+            acc += f_lo @ w_hi.T
+        out += sign * acc
+    return out

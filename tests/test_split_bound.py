@@ -25,7 +25,7 @@ import numpy as np
 import pytest
 
 from paper_2304_14492_gb300 import synth
-from splitmath import rne, split_moments, terms
+from splitmath import dft_matrix, dft_split_spectra, rne, split_moments, terms
 
 
 WORKLOADS = {
@@ -62,3 +62,52 @@ def test_weaker_bf16_splits_break_the_bound(workload, weaker):
     a, f, z, S = workload
     err = np.abs(split_moments(a, f, 8, **weaker) - z)
     assert np.max(err / (3 * 2.0 ** -18 * S)) > 1.0
+
+
+# ---- the angular sums as a split product (the tensor-core DFT kernel)
+#
+# F_m(rho_i) = sum_k f_ik w_mk with |w_mk| = 1; the split drops at most
+# 3 u^2 |f_ik| per term (same argument as above, per real component, and the
+# two components together stay inside it by the triangle inequality), so
+#
+#     |F_split - F| <= 3 u^2 sum_k |f_ik|.
+
+DFT_WORKLOADS = {
+    "64x64 uniform, N_theta 64": (lambda: synth.uniform_image(64, 64, workload=0, index=0), (20, 32, 64)),
+    "512x512 blobs, N_theta 256": (lambda: synth.blob_image(512, 512, 8, workload=1, index=0), (50, 256, 256)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(DFT_WORKLOADS))
+def dft_workload(request):
+    from oracle import grid, moments as om, resample
+    make, (n_max, n_rho, n_theta) = DFT_WORKLOADS[request.param]
+    img = make().astype(np.float64)
+    rho, _ = grid.radial_nodes(n_rho)
+    fh = resample.polar_resample(img, rho, n_theta, grid.default_geometry(*img.shape))
+    return fh, n_max, om.angular_dft(fh, n_max), np.sum(np.abs(fh), axis=1)[:, None]
+
+
+def test_dft_matrix_is_the_oracles_angular_transform(dft_workload):
+    fh, n_max, F, _ = dft_workload
+    c, s = dft_matrix(n_max, fh.shape[1])
+    assert np.allclose(fh @ c.T + 1j * (fh @ s.T), F, rtol=0, atol=1e-12 * np.max(np.abs(F)))
+
+
+@pytest.mark.parametrize("p", [8, 11])
+def test_dft_split_stays_inside_its_bound(dft_workload, p):
+    fh, n_max, F, L1 = dft_workload
+    err = np.abs(dft_split_spectra(fh, n_max, p) - F)
+    assert np.all(err <= 3 * 2.0 ** (-2 * p) * L1), float(np.max(err / (3 * 2.0 ** (-2 * p) * L1)))
+
+
+# The bound adds every term's worst case; the rounding errors of the N_theta
+# terms have mixed signs, so the real split sits at a few percent of it, and
+# of the weaker splits only a lo part of 2 bits or a dropped cross term
+# exceeds it (the GPU test of the kernel compares it with this emulation to
+# FP32 rounding, which catches the rest).
+@pytest.mark.parametrize("weaker", [dict(lo_bits=2), dict(terms_kept=("hh", "hl")), dict(terms_kept=("hh",))])
+def test_weaker_dft_splits_break_the_bound(dft_workload, weaker):
+    fh, n_max, F, L1 = dft_workload
+    err = np.abs(dft_split_spectra(fh, n_max, 8, **weaker) - F)
+    assert np.max(err / (3 * 2.0 ** -16 * L1)) > 1.0
