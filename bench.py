@@ -966,7 +966,7 @@ def profile_pass(batch=16):
     """Every kernel path of the library once, at the bench's sizes where it has
     one: plan builds, the FP32 and FP16 projection forms on 16 4K frames (the
     stage calls and the tile path), the fused resampling + ring FFT kernel and
-    the tensor-core DFT kernel on the same frames, the gather path (frames TMA cannot stage), the FP32
+    the two tensor-core DFT kernels on the same frames, the gather path (frames TMA cannot stage), the FP32
     reconstruction with errors, pixel reconstruction and normalisation (a
     colour frame), the upload
     of host frames, the Cartesian route at 4000 x 4000, an uneven batch and a
@@ -1009,12 +1009,13 @@ def profile_pass(batch=16):
         torch.cuda.synchronize(dev)
         zm.zm_plan_destroy(plan)
     del os.environ["ZM_FUSED"]
-    os.environ["ZM_RING_DFT"] = "1"              # the tensor-core DFT kernel (opt-in) on the same frames
-    plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
-    zm.zm_moments(plan, views, out)
-    torch.cuda.synchronize(dev)
-    zm.zm_plan_destroy(plan)
-    del os.environ["ZM_RING_DFT"]
+    for var in ("ZM_RING_DFT", "ZM_POLAR_DFT"):   # the two tensor-core DFT kernels (opt-in) on the same frames
+        os.environ[var] = "1"
+        plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
+        zm.zm_moments(plan, views, out)
+        torch.cuda.synchronize(dev)
+        zm.zm_plan_destroy(plan)
+        del os.environ[var]
     plan = zm.zm_plan(N_MAX, N_RHO, N_THETA, zm.ZM_PREC_BF16X3)
     bench_colour(zm, torch, dev, plan, P, steps=1)
     zm.zm_plan_destroy(plan)

@@ -158,7 +158,10 @@ int zm_plan_nodes(zm_plan_t plan, double* rho, double* wr, void* stream);
  * angular sums of Eq. 1 as a product with the DFT matrix on the tensor cores
  * (split operands, FP32 accumulation; moments within the split bar of the
  * FFT paths, not bit-equal to them); it is off by default, being slower than
- * the tile path on the 4K frame.
+ * the tile path on the 4K frame.  ZM_POLAR_DFT=1 likewise sends the angular
+ * transform of polar samples (the tile path's resampled samples, and
+ * zm_moments_polar) of such plans to a tensor-core DFT instead of the radix
+ * ring FFT; also off by default (no faster on the 4K frame).
  * Errors: ZM_EINVAL (batch < 1, null pointers, image < 1x1, bad pitch),
  * ZM_ENOMEM (workspace growth), ZM_ECUDA.
  */

@@ -573,10 +573,12 @@ static int launch_gather(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, in
     return ZM_OK;
 }
 
-// Ring FFT of given polar samples fhat[b][i][k] -> F for images [b0, b0 + nb)
-// of a batch of `batch`.
+// Angular transform of given polar samples fhat[b][i][k] -> F (or the
+// operand blocks Fblk) for images [b0, b0 + nb) of a batch of `batch`: the
+// tensor-core DFT where the plan allows it, else the ring FFT.
 static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int batch, float* F, uint8_t* Fblk,
                             cudaStream_t st) {
+    if (Fblk && polar_dft_eligible(p, fhat)) return launch_polar_dft(p, fhat, b0, nb, batch, Fblk, st);
     const int R = Fblk ? 8 : pick_rings(p, batch);
     static thread_local KbParams kp;
     kp.Fblk = Fblk;

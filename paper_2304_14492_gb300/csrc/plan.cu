@@ -393,6 +393,7 @@ static void free_plan(zm_plan_t p) {
     release_fused(p);
     release_dft(p);
     cudaFree(p->dft);
+    cudaFree(p->dft32);
     cudaFree(p->rho32);
     cudaFree(p->A32);
     cudaFree(p->R32m);
@@ -473,6 +474,7 @@ extern "C" int zm_plan(zm_plan_t* plan, int n_max, int n_rho, int n_theta, unsig
     p->prec = prec == ZM_PREC_BF16X3 ? PREC_BF16X3 : prec == ZM_PREC_FP16X3 ? PREC_FP16X3 : PREC_FP32;
     if (const char* f = std::getenv("ZM_FUSED")) p->fused_mode = (f[0] == '1') ? 1 : (f[0] == '0') ? -1 : 0;
     if (const char* f = std::getenv("ZM_RING_DFT")) p->dft_mode = (f[0] == '1') ? 1 : 0;
+    if (const char* f = std::getenv("ZM_POLAR_DFT")) p->pdft_mode = (f[0] == '1') ? 1 : 0;
     int st = acquire_table(p->device, (int)grid, n_rho, n_max, &p->table);
     if (st == ZM_OK) st = build_plan_tables(p);
     if (st != ZM_OK) {

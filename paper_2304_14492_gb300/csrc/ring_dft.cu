@@ -36,6 +36,7 @@
 #include <tuple>
 #include <vector>
 
+#include "dft_tiles.cuh"
 #include "tc_common.cuh"
 #include "zm_internal.cuh"
 
@@ -76,12 +77,6 @@ struct DfParams {
     const float* data[DF_MAX_IMG];
     long long pitch[DF_MAX_IMG];
 };
-
-// byte offset of element (row, k) in a 16-deep K-major tile: 8-row groups of
-// two core matrices (8 rows x 16 bytes each, 128 bytes apart along K)
-__host__ __device__ inline uint32_t tile16_off(int row, int k) {
-    return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
 
 __device__ __forceinline__ void df_cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -305,7 +300,7 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_ring_dft(const __grid_constan
             lv[q] = __bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
         }
         uint8_t* at = atiles + (g & 1) * 2 * DF_ATILE;
-        const uint32_t o = tile16_off(row, 4 * kq);
+        const uint32_t o = dft_tile_off<DF_K>(row, 4 * kq);
         *reinterpret_cast<uint2*>(at + o) = make_uint2(hv[0], hv[1]);
         *reinterpret_cast<uint2*>(at + DF_ATILE + o) = make_uint2(lv[0], lv[1]);
     }
@@ -387,31 +382,6 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_ring_dft(const __grid_constan
         const size_t off = fblk_row(m, ring0, 2 * b + c, p.n_chunks, ncol);
         *reinterpret_cast<uint4*>(p.Fblk + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
         *reinterpret_cast<uint4*>(p.Fblk + p.fblk_half + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-    }
-}
-
-// DFT tiles of a plan: chunk c, half h, row j (j < ncols: cos of m = j, else
-// -sin of m = j - ncols; zero for m > n_max), k = 0..15: the angle index
-// (m (16 c + k)) mod N, evaluated in FP64 and split into bf16 hi + lo.
-__global__ void k_build_dft(int n_theta, int n_max, int ncols, uint8_t* __restrict__ out) {
-    const int c = blockIdx.x;
-    const int ncol2 = 2 * ncols;
-    const size_t bt = (size_t)ncol2 * DF_K * 2;
-    for (int e = threadIdx.x; e < ncol2 * DF_K; e += blockDim.x) {
-        const int j = e / DF_K, k = e - j * DF_K;
-        const int m = j < ncols ? j : j - ncols;
-        double w = 0.0;
-        if (m <= n_max) {
-            const long long idx = ((long long)m * (DF_K * c + k)) % n_theta;
-            double sn, cn;
-            sincospi(2.0 * (double)idx / n_theta, &sn, &cn);
-            w = j < ncols ? cn : -sn;
-        }
-        const __nv_bfloat16 hi = __double2bfloat16(w);
-        const __nv_bfloat16 lo = __double2bfloat16(w - (double)__bfloat162float(hi));
-        const uint32_t o = tile16_off(j, k);
-        *reinterpret_cast<__nv_bfloat16*>(out + (size_t)c * 2 * bt + o) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(out + (size_t)c * 2 * bt + bt + o) = lo;
     }
 }
 
@@ -540,14 +510,12 @@ void release_dft(zm_plan_t p) {
     }
 }
 
-// The plan's DFT tiles (built on first use; freed with the plan).
+// The plan's 16-deep DFT tiles (built on first use; freed with the plan).
 static int dft_table(zm_plan_t p) {
     if (p->dft) return ZM_OK;
-    const int ncols = 8 * ((p->n_max + 1 + 7) / 8);
-    const size_t bytes = (size_t)(p->n_theta / DF_K) * 2 * (size_t)(2 * ncols) * DF_K * 2;
-    ZM_CUDA_TRY(cudaMalloc(&p->dft, bytes));
-    k_build_dft<<<p->n_theta / DF_K, 256>>>(p->n_theta, p->n_max, ncols, p->dft);
-    ZM_LAUNCH_CHECK("k_build_dft");
+    ZM_CUDA_TRY(cudaMalloc(&p->dft, dft_table_bytes<DF_K>(p->n_theta, p->n_max)));
+    k_build_dft_tiles<DF_K><<<p->n_theta / DF_K, 256>>>(p->n_theta, p->n_max, dft_ncols(p->n_max), p->dft);
+    ZM_LAUNCH_CHECK("k_build_dft_tiles");
     ZM_CUDA_TRY(cudaDeviceSynchronize());
     return ZM_OK;
 }
@@ -580,7 +548,7 @@ int launch_ring_dft(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int bat
     if (!dp->ok) return ZM_EUNSUPPORTED;
     int s = dft_table(p);
     if (s != ZM_OK) return s;
-    const int ncols = 8 * ((p->n_max + 1 + 7) / 8);
+    const int ncols = dft_ncols(p->n_max);
     const size_t smem = DfSmem::bytes(2 * ncols, dp->nstage);
     if (smem > 227 * 1024) return ZM_EUNSUPPORTED;
     static size_t configured[64] = {0};

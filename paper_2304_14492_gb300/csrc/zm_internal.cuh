@@ -212,6 +212,13 @@ struct zm_plan_s {
     // from the environment variable ZM_RING_DFT ("1") at plan creation
     int dft_mode = 0;
     uint8_t* dft = nullptr;     // its DFT tiles (bf16 hi / lo), built on first use
+    // the angular sums from polar samples on the tensor cores (polar_dft.cu),
+    // bf16 plans with the blocked projection and n_max <= 127: 1 = wherever it
+    // applies, else never (the default: the radix ring FFT measured as fast on
+    // the 4K frame, and the zm_moments step faster with it); set from the
+    // environment variable ZM_POLAR_DFT ("1") at plan creation
+    int pdft_mode = 0;
+    uint8_t* dft32 = nullptr;   // its 32-deep DFT tiles, built on first use
 };
 
 namespace zm {
@@ -318,5 +325,10 @@ void release_fused(zm_plan_t p);
 bool dft_eligible(zm_plan_t p, const zm_image_t& im);
 int launch_ring_dft(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, int batch, uint8_t* Fblk, cudaStream_t st);
 void release_dft(zm_plan_t p);
+
+// The angular sums from polar samples as a tensor-core DFT (polar_dft.cu):
+// writes the blocked projection's operand blocks
+bool polar_dft_eligible(zm_plan_t p, const float* fhat);
+int launch_polar_dft(zm_plan_t p, const float* fhat, int b0, int nb, int batch, uint8_t* Fblk, cudaStream_t st);
 
 }  // namespace zm

@@ -38,6 +38,7 @@ def _fused(monkeypatch):
     # plans made in these tests fuse wherever the geometry fits, whatever
     # their size (the library's automatic choice fuses small grids only)
     monkeypatch.setenv("ZM_FUSED", "1")
+    monkeypatch.delenv("ZM_POLAR_DFT", raising=False)
 
 
 def dev(a):
