@@ -67,7 +67,7 @@ struct PdParams {
 
 __host__ __device__ inline size_t pd_btile(int ncol2) { return (size_t)ncol2 * PD_K * 2; }   // one half
 inline size_t pd_smem_bytes(int ncol2) {
-    return (size_t)PD_AREGION + (size_t)PD_NB * 2 * pd_btile(ncol2) + 8 * (2 * PD_NA + 2 * PD_NB) + 16;
+    return (size_t)PD_AREGION + (size_t)PD_NB * 2 * pd_btile(ncol2) + 8 * (2 * PD_NA + PD_NB) + 16;
 }
 
 __device__ __forceinline__ void pd_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -96,15 +96,16 @@ __global__ void __launch_bounds__(PD_THREADS, 1) k_polar_dft(const __grid_consta
     uint8_t* areg = psm;                                          // [slot][hi, lo][8 KB]
     uint8_t* breg = psm + PD_AREGION;                             // [slot][hi, lo][bt]
     uint64_t* bars = reinterpret_cast<uint64_t*>(breg + PD_NB * 2 * bt);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * PD_NA + 2 * PD_NB);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * PD_NA + PD_NB);
     volatile int* okflag = reinterpret_cast<volatile int*>(tslot + 1);
     const uint32_t bar0 = smem_u32(bars);
-    // A slots: full (16 producer warps arrive), done (MMA commit); B slots:
-    // full (bulk copy), done (MMA commit)
-    auto bar_afull = [&](int slot) { return bar0 + 8u * (uint32_t)slot; };
+    // per A slot: "full" (the stage's A tile and DFT tiles are in: 16 producer
+    // warps and the tile copier arrive, the copy's bytes complete it) and
+    // "done" (MMA commit); per B slot: "done" (MMA commit).  One barrier for
+    // both tiles: the MMA thread's waits are on its critical path.
+    auto bar_full = [&](int slot) { return bar0 + 8u * (uint32_t)slot; };
     auto bar_adone = [&](int slot) { return bar0 + 8u * (uint32_t)(PD_NA + slot); };
-    auto bar_bfull = [&](int slot) { return bar0 + 8u * (uint32_t)(2 * PD_NA + slot); };
-    auto bar_bdone = [&](int slot) { return bar0 + 8u * (uint32_t)(2 * PD_NA + PD_NB + slot); };
+    auto bar_bdone = [&](int slot) { return bar0 + 8u * (uint32_t)(2 * PD_NA + slot); };
 
     const int tile = blockIdx.x % p.ntile;
     const int b = p.b_off + blockIdx.x / p.ntile;
@@ -116,11 +117,10 @@ __global__ void __launch_bounds__(PD_THREADS, 1) k_polar_dft(const __grid_consta
     }
     if (tid == 0) {
         for (int k = 0; k < PD_NA; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_afull(k)), "r"(PD_PROD / 32));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_full(k)), "r"(PD_PROD / 32 + 1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_adone(k)));
         }
         for (int k = 0; k < PD_NB; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_bfull(k)));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_bdone(k)));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -160,11 +160,15 @@ __global__ void __launch_bounds__(PD_THREADS, 1) k_polar_dft(const __grid_consta
                 const int s = s0 + 2 * h;
                 if (s >= ns || !ok) break;                    // warp-uniform
                 // the pair's slots were read by the MMAs of stages s - NA and
-                // s + 1 - NA.  Every lane waits, then the warp decides together.
-                bool w = true;
-                for (int st = min(s + 1, ns - 1); st >= s && w; --st)
-                    if (st >= PD_NA) w = mbar_wait(bar_adone(st % PD_NA), (uint32_t)((st / PD_NA) - 1) & 1u, t0);
-                if (!__all_sync(0xffffffffu, w)) {
+                // s + 1 - NA.  Lane 0 waits (512 threads polling one barrier
+                // word serialise), the warp's barrier orders the other lanes'
+                // stores after it, and the warp decides together.
+                int w = 1;
+                if (lane == 0)
+                    for (int st = min(s + 1, ns - 1); st >= s && w; --st)
+                        if (st >= PD_NA) w = mbar_wait(bar_adone(st % PD_NA), (uint32_t)((st / PD_NA) - 1) & 1u, t0);
+                __syncwarp();
+                if (!__shfl_sync(0xffffffffu, w, 0)) {
                     ok = false;
                     if (lane == 0) {
                         *okflag = 0;
@@ -191,8 +195,8 @@ __global__ void __launch_bounds__(PD_THREADS, 1) k_polar_dft(const __grid_consta
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // A tiles -> tensor core
                 __syncwarp();
                 if (lane == 0) {
-                    pd_arrive(bar_afull(s % PD_NA));
-                    if (s + 1 < ns) pd_arrive(bar_afull((s + 1) % PD_NA));
+                    pd_arrive(bar_full(s % PD_NA));
+                    if (s + 1 < ns) pd_arrive(bar_full((s + 1) % PD_NA));
                 }
             }
         }
@@ -202,8 +206,7 @@ __global__ void __launch_bounds__(PD_THREADS, 1) k_polar_dft(const __grid_consta
         const uint32_t idesc = instr_desc(p.ncol2, 0);
         int n_issued = 0;
         auto ready = [&](int s) {
-            return mbar_wait(bar_bfull(s % PD_NB), (uint32_t)(s / PD_NB) & 1u, t0) &&
-                   mbar_wait(bar_afull(s % PD_NA), (uint32_t)(s / PD_NA) & 1u, t0);
+            return mbar_wait(bar_full(s % PD_NA), (uint32_t)(s / PD_NA) & 1u, t0);
         };
         bool ok = ns == 0 || ready(0);
         for (int s = 0; s < ns && ok; ++s) {
@@ -252,21 +255,23 @@ __global__ void __launch_bounds__(PD_THREADS, 1) k_polar_dft(const __grid_consta
                 ok = false;
                 break;
             }
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_bfull(slot)),
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_full(s % PD_NA)),
                          "r"((uint32_t)(2 * bt))
                          : "memory");
-            bulk_copy(smem_u32(breg + slot * 2 * bt), p.dft + (size_t)s * 2 * bt, (uint32_t)(2 * bt), bar_bfull(slot));
+            bulk_copy(smem_u32(breg + slot * 2 * bt), p.dft + (size_t)s * 2 * bt, (uint32_t)(2 * bt), bar_full(s % PD_NA));
             ++n_fetched;
         }
         if (!ok) {
             *okflag = 0;
             atomicExch(p.status, ZM_ETIMEOUT);
-            // the copies in flight land before the kernel ends (one phase at
-            // most outstanding per slot: a slot is refilled after its reader)
+            // the copies in flight land before the kernel ends: wait (bounded)
+            // for the "full" phase of the last stage fetched into each A slot
+            // (one phase at most outstanding: a stage is fetched after the
+            // MMAs of the slot's previous stage completed)
             const unsigned long long t1 = global_ns();
-            for (int k = 0; k < PD_NB; ++k) {
-                const int cb = (n_fetched + PD_NB - 1 - k) / PD_NB;
-                if (cb > 0) mbar_wait(bar_bfull(k), (uint32_t)(cb - 1) & 1u, t1);
+            for (int k = 0; k < PD_NA; ++k) {
+                const int cb = (n_fetched + PD_NA - 1 - k) / PD_NA;
+                if (cb > 0) mbar_wait(bar_full(k), (uint32_t)(cb - 1) & 1u, t1);
             }
         }
     }
