@@ -29,6 +29,7 @@ struct KbParams {
     float* F;              // [n_max+1][batch_total][2][n_rho]
     float* fhat_out;       // [batch_total][n_rho][N] or NULL
     const float* fhat_in;  // [batch_total][n_rho][N] (polar input mode)
+    int discard_in;        // fhat_in is the plan's scratch: its L2 lines are dropped once read
     GeoImage img[KB_MAX_IMG];
 };
 
@@ -256,6 +257,17 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_blk(const __
         const int i0 = rb * R;
         for (int q = 0; q < 4; ++q) {
             FFT::fwd(v, lane, twt, X);
+            if constexpr (N >= 32) {
+                // the ring's samples are in the registers now: when they are the
+                // plan's scratch, their L2 lines are invalidated without a write
+                // back (every line of a ring row belongs to that ring alone)
+                const int b = (g0 + gi) * 4 + q;
+                if (p.discard_in && i0 + warp < n_rho && in_run(b)) {
+                    const char* base = reinterpret_cast<const char*>(p.fhat_in + ((size_t)b * n_rho + i0 + warp) * N);
+                    for (int l = lane; l < N / 32; l += 32)
+                        asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + 128 * l) : "memory");
+                }
+            }
             if (lane < FFT::L) {
 #pragma unroll
                 for (int r = 0; r < FFT::Q; ++r) X[FFT::pad(FFT::fwd_index(r, lane))] = v[r];
@@ -562,6 +574,7 @@ static int launch_gather(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, in
     kp.F = F;
     kp.fhat_out = fhat_out;
     kp.fhat_in = nullptr;
+    kp.discard_in = 0;
     for (int c0 = b0; c0 < b0 + nb; c0 += KB_MAX_IMG) {
         const int nc = std::min(KB_MAX_IMG, b0 + nb - c0);
         kp.b_off = c0;
@@ -577,7 +590,7 @@ static int launch_gather(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, in
 // operand blocks Fblk) for images [b0, b0 + nb) of a batch of `batch`: the
 // tensor-core DFT where the plan allows it, else the ring FFT.
 static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int batch, float* F, uint8_t* Fblk,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool scratch = false) {
     if (Fblk && polar_dft_eligible(p, fhat)) return launch_polar_dft(p, fhat, b0, nb, batch, Fblk, st);
     const int R = Fblk ? 8 : pick_rings(p, batch);
     static thread_local KbParams kp;
@@ -593,6 +606,7 @@ static int launch_polar_fft(zm_plan_t p, const float* fhat, int b0, int nb, int 
     kp.F = F;
     kp.fhat_out = nullptr;
     kp.fhat_in = fhat;
+    kp.discard_in = scratch && Fblk && ((uintptr_t)fhat & 127u) == 0 ? 1 : 0;
     for (int c0 = b0; c0 < b0 + nb; c0 += 65535) {
         const int nc = std::min(65535, b0 + nb - c0);
         kp.b_off = c0;
@@ -652,8 +666,11 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
                 if (s != ZM_OK) return s;
                 fh = (float*)p->ws_fhat.ptr;
             }
-            s = launch_resample_tiles(p, imgs, b, e - b, fh, st);
-            if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, Fblk, st);
+            // the plan's scratch (no caller buffer): the samples are kept in L2
+            // for the ring FFT, which drops them once read
+            const bool scratch = fh != fhat_out && !resample_only;
+            s = launch_resample_tiles(p, imgs, b, e - b, fh, st, scratch);
+            if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, Fblk, st, scratch);
         } else {
             while (e < batch && !use_tma(e)) ++e;
             s = launch_gather(p, imgs, b, e - b, batch, F, fhat_out, resample_only, Fblk, st);

@@ -89,6 +89,7 @@ struct TileParams {
     float* fhat;
     int* status;
     int n_rho, N, b_off;
+    int keep_l2;                 // fhat is scratch the next kernel reads: stores marked evict_last
     int nb;                      // images in this launch
     CUtensorMap maps[TILE_MAX_IMG];
 };
@@ -211,7 +212,7 @@ __device__ __forceinline__ void tile_group(const int4* rec, int cnt, int c0, int
 }
 
 __device__ __forceinline__ void tile_interp(const float* tile, float* out, const int4 (&ts)[TILE_G],
-                                            const bool (&on)[TILE_G]) {
+                                            const bool (&on)[TILE_G], uint64_t pol) {
     float val[TILE_G];
 #pragma unroll
     for (int k = 0; k < TILE_G; ++k) {
@@ -224,7 +225,8 @@ __device__ __forceinline__ void tile_interp(const float* tile, float* out, const
     }
 #pragma unroll
     for (int k = 0; k < TILE_G; ++k)
-        if (on[k]) out[ts[k].y] = val[k];
+        if (on[k]) asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(out + ts[k].y), "f"(val[k]), "l"(pol)
+                                : "memory");
 }
 
 __device__ __forceinline__ bool tile_try_wait(uint32_t bar) {
@@ -294,14 +296,17 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB) k_resample_tiles(cons
 
     const size_t img_stride = (size_t)p.n_rho * p.N;
     float* out = p.fhat + ((size_t)(p.b_off + b0) * p.n_rho + it.i_lo) * p.N;
+    uint64_t spol;
+    if (p.keep_l2) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(spol));
+    else asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(spol));
 #pragma unroll
     for (int k = 0; k < TILE_IPC; ++k)
-        if (k < nimg) tile_interp(tile_sm + k * TILE_BOX_FLOATS, out + k * img_stride, ts, on);
+        if (k < nimg) tile_interp(tile_sm + k * TILE_BOX_FLOATS, out + k * img_stride, ts, on, spol);
     for (int c0 = TILE_G * TILE_THREADS; c0 < cnt; c0 += TILE_G * TILE_THREADS) {
         tile_group(rec, cnt, c0, ts, on);
 #pragma unroll
         for (int k = 0; k < TILE_IPC; ++k)
-            if (k < nimg) tile_interp(tile_sm + k * TILE_BOX_FLOATS, out + k * img_stride, ts, on);
+            if (k < nimg) tile_interp(tile_sm + k * TILE_BOX_FLOATS, out + k * img_stride, ts, on, spol);
     }
 }
 
@@ -516,7 +521,8 @@ static int get_tiles(zm_plan_t p, const GeoImage& g, TileList** out) {
 
 // Resample images [b0, b0 + nb) (all TMA-eligible, one geometry) into
 // fhat[b][i][k] (fhat points at image 0 of the whole batch).
-int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st) {
+int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st,
+                          bool keep_l2) {
     const GeoImage g = resolve(imgs[b0]);
     TileList* tl = nullptr;
     int s = get_tiles(p, g, &tl);
@@ -529,6 +535,7 @@ int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, f
     tp.recs = tl->recs;
     tp.fhat = fhat;
     tp.status = p->status;
+    tp.keep_l2 = keep_l2 ? 1 : 0;
     tp.n_rho = p->n_rho;
     tp.N = p->n_theta;
     for (int c0 = 0; c0 < nb; c0 += TILE_MAX_IMG) {

@@ -309,7 +309,10 @@ int check_images(const zm_image_t* imgs, int batch);
 // Cartesian-tile resampling (resample_tiles.cu)
 bool tma_eligible(const zm_image_t& im);
 bool same_geometry(const zm_image_t& a, const zm_image_t& b);
-int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st);
+// keep_l2: fhat is scratch that the next kernel reads (stored with an L2
+// evict_last policy)
+int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, float* fhat, cudaStream_t st,
+                          bool keep_l2 = false);
 void release_tiles(zm_plan_t p);
 
 // Resampling fused with the ring FFT (ring_fused.cu): polar samples stay on chip
