@@ -80,25 +80,23 @@ struct UpParams {
     UpBox box[UP_MAX_IMG];
 };
 
-// blockIdx.y = box, blockIdx.x strides rows; thread 0 finds a row's span and
-// the block copies it.  Rows whose host start is 16-byte aligned (and pitch a
-// multiple of 4) move as float4 with four loads in flight per thread: the host
-// link has a long latency, so many bytes must be in flight; the rest of a row
-// takes the scalar loop.
+// blockIdx.y = box; each warp copies whole rows (row = warp index over the
+// grid's warps, strided): lane 0 finds the row's span (the FP64 arithmetic of
+// disk_row_span) and broadcasts it, and the warp copies it.  Eight rows per
+// block are in flight at once, with no block barrier between rows; rows whose
+// host start is 16-byte aligned (and pitch a multiple of 4) move as float4
+// with four loads in flight per lane: the host link has a long latency, so
+// many bytes must be in flight.  The rest of a row takes the scalar loop.
 __global__ void __launch_bounds__(256) k_upload_boxes(const __grid_constant__ UpParams p) {
     const UpBox bx = p.box[blockIdx.y];
-    __shared__ int span[2];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
     const bool vec = ((reinterpret_cast<uintptr_t>(bx.src) & 15u) == 0) && (bx.spitch & 3) == 0;
-    for (int y = blockIdx.x; y < bx.h; y += gridDim.x) {
-        __syncthreads();                       // span[] of the previous row is read
-        if (threadIdx.x == 0) {
-            int s0 = 0, e0 = -1;
-            if (!box_row_copy(y, bx.x0, bx.y0, bx.w, bx.cx, bx.cy, bx.r, &s0, &e0)) e0 = -1;
-            span[0] = s0;
-            span[1] = e0;
-        }
-        __syncthreads();
-        const int x_s = span[0], x_e = span[1];
+    for (int y = blockIdx.x * wpb + (threadIdx.x >> 5); y < bx.h; y += gridDim.x * wpb) {
+        int x_s = 0, x_e = -1;
+        if (lane == 0 && !box_row_copy(y, bx.x0, bx.y0, bx.w, bx.cx, bx.cy, bx.r, &x_s, &x_e)) x_e = -1;
+        x_s = __shfl_sync(0xffffffffu, x_s, 0);
+        x_e = __shfl_sync(0xffffffffu, x_e, 0);
         if (x_e < x_s) continue;
         const float* s = bx.src + (long long)y * bx.spitch + x_s;
         float* d = p.dev + bx.dst + (long long)y * bx.dpitch + x_s;
@@ -108,22 +106,22 @@ __global__ void __launch_bounds__(256) k_upload_boxes(const __grid_constant__ Up
             const int n4 = n >> 2;
             const float4* s4 = reinterpret_cast<const float4*>(s);
             float4* d4 = reinterpret_cast<float4*>(d);
-            for (int x0 = threadIdx.x; x0 < n4; x0 += 4 * blockDim.x) {
+            for (int x0 = lane; x0 < n4; x0 += 4 * 32) {
                 float4 v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int x = x0 + u * blockDim.x;
+                    const int x = x0 + u * 32;
                     if (x < n4) v[u] = s4[x];
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int x = x0 + u * blockDim.x;
+                    const int x = x0 + u * 32;
                     if (x < n4) d4[x] = v[u];
                 }
             }
             done = n4 << 2;
         }
-        for (int x = done + threadIdx.x; x < n; x += blockDim.x) d[x] = s[x];
+        for (int x = done + lane; x < n; x += 32) d[x] = s[x];
     }
 }
 
@@ -240,11 +238,11 @@ extern "C" int zm_upload_disk(const zm_image_t* host_imgs, int batch, float* dev
             max_h = std::max(max_h, bx.h);
         }
         up.n = nc;
-        // about two blocks per SM in all: many more bytes in flight than the
-        // host link's latency needs, while SMs stay free for kernels that run
-        // beside the upload on other streams
+        // about two blocks (16 rows in flight) per SM in all: many more bytes in
+        // flight than the host link's latency needs, while SMs stay free for
+        // kernels that run beside the upload on other streams
         const int per = std::max(4, 2 * num_sms(device) / nc);
-        k_upload_boxes<<<dim3(std::min(max_h, per), nc), 256, 0, (cudaStream_t)stream>>>(up);
+        k_upload_boxes<<<dim3(std::min((max_h + 7) / 8, per), nc), 256, 0, (cudaStream_t)stream>>>(up);
         ZM_LAUNCH_CHECK("k_upload_boxes");
     }
     return ZM_OK;
