@@ -46,7 +46,7 @@ extern "C" {
 #define ZM_ENOMEM        2  /* device allocation failed or budget exceeded   */
 #define ZM_ECUDA         3  /* CUDA launch / API error (detail kept)         */
 #define ZM_ETIMEOUT      4  /* a bounded wait ran out                        */
-#define ZM_EUNSUPPORTED  5  /* valid request this build does not implement   */
+#define ZM_EUNSUPPORTED  5  /* valid request the library does not implement  */
 
 /* ---- plan flags (zm_plan) ---------------------------------------------- */
 #define ZM_GRID_MIDPOINT 0x0u   /* rho_i = (i + 1/2)/N_rho, weight rho_i/N_rho */
