@@ -16,12 +16,13 @@
 // loads, four stages ahead in registers, splits them and stores one 16-byte
 // core-matrix row of the hi tile and one of the lo tile; stages go in pairs
 // (one slot wait, one proxy fence per pair), after which a warp's lane 0
-// arrives on both stages' "A full" barriers.  Warp 16 (lane 0) issues the
-// six MMAs of a stage once its A and B tiles are in and commits them to the
-// "done" barriers of the stage's A slot and B slot; an MMA issue blocks while
-// the tensor pipe is busy, so this thread does nothing else.  Warp 17 (lane 0)
-// bulk-copies each stage's DFT tiles into its B slot once the slot's previous
-// MMAs are done.  Eight A slots and three B slots: a slot's round trip
+// arrives on both stages' "full" barriers.  Warp 17 (lane 0) bulk-copies each
+// stage's DFT tiles into its B slot once the slot's previous MMAs are done;
+// the copy arrives on the same "full" barrier (17 arrivals and the copy's
+// bytes complete it).  Warp 16 (lane 0) issues the six MMAs of a stage once
+// that barrier completes and commits them to the "done" barriers of the
+// stage's A slot and B slot; an MMA issue blocks while the tensor pipe is
+// busy, so this thread does nothing else.  Eight A slots and three B slots: a slot's round trip
 // (written, fenced, read by the MMAs, seen done) spans several stages, and
 // with fewer slots the producers and the tensor core took turns.  Every wait is
 // bounded (2 s from the kernel's start); one that runs out sets the plan's
