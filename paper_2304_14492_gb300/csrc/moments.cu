@@ -667,9 +667,11 @@ int launch_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
                 fh = (float*)p->ws_fhat.ptr;
             }
             // the plan's scratch (no caller buffer): the samples are kept in L2
-            // for the ring FFT, which drops them once read
+            // for the ring FFT, which drops them once read (not for the opt-in
+            // tensor-core DFT, which does not)
             const bool scratch = fh != fhat_out && !resample_only;
-            s = launch_resample_tiles(p, imgs, b, e - b, fh, st, scratch);
+            const bool keep = scratch && !(Fblk && polar_dft_eligible(p, fh));
+            s = launch_resample_tiles(p, imgs, b, e - b, fh, st, keep);
             if (s == ZM_OK && !resample_only) s = launch_polar_fft(p, fh, b, e - b, batch, F, Fblk, st, scratch);
         } else {
             while (e < batch && !use_tma(e)) ++e;
