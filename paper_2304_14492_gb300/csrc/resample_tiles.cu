@@ -251,7 +251,9 @@ __device__ __forceinline__ bool tile_wait(uint32_t bar) {
 
 // One CTA per (item, TILE_IPC images): the boxes of its images arrive by TMA
 // while the threads load the records of their first samples, which then serve
-// every image; the rest of a heavy item follows in groups.
+// every image; the rest of a heavy item follows in groups.  Launched as a
+// programmatic dependent: the record loads start before the previous kernel
+// has finished, the boxes (and every store) after.
 __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB) k_resample_tiles(const __grid_constant__ TileParams p) {
     extern __shared__ __align__(128) float tile_sm[];          // [TILE_IPC][TILE_BOX_FLOATS]
     __shared__ __align__(8) uint64_t bar[TILE_IPC];
@@ -261,10 +263,24 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB) k_resample_tiles(cons
     const int nimg = min(TILE_IPC, p.nb - b0);
     const uint32_t bar_a = static_cast<uint32_t>(__cvta_generic_to_shared(&bar[0]));
     const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(tile_sm));
+    // this thread's first samples: the records belong to the plan (written
+    // before any launch), so their loads go out before the wait below and
+    // overlap the previous kernel's end
+    const int cnt = it.cnt;
+    const int4* rec = p.recs + it.s0;
+    int4 ts[TILE_G];
+    bool on[TILE_G];
+    tile_group(rec, cnt, 0, ts, on);
     if (threadIdx.x == 0) {
         for (int k = 0; k < nimg; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a + 8u * k));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    // the images may come from the previous kernel, and it may still read
+    // f_hat.  (No early launch of the dependents: the ring FFT's CTAs would
+    // take SM room from this kernel's later waves.)
+    griddep_wait();
+    if (threadIdx.x == 0) {
         uint64_t pol;
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
         for (int k = 0; k < nimg; ++k) {
@@ -277,12 +293,6 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MINB) k_resample_tiles(cons
                 : "memory");
         }
     }
-    // while the boxes are in flight: this thread's first samples
-    const int cnt = it.cnt;
-    const int4* rec = p.recs + it.s0;
-    int4 ts[TILE_G];
-    bool on[TILE_G];
-    tile_group(rec, cnt, 0, ts, on);
     // one thread waits for the boxes (bounded); the others wait at the barrier
     if (threadIdx.x == 0) {
         bool ok = true;
@@ -559,8 +569,8 @@ int launch_resample_tiles(zm_plan_t p, const zm_image_t* imgs, int b0, int nb, f
                 if (dev >= 0 && dev < 64) configured[dev] = true;
             }
         }
-        k_resample_tiles<<<dim3(tl->n, (nc + TILE_IPC - 1) / TILE_IPC), TILE_THREADS, smem, st>>>(tp);
-        ZM_LAUNCH_CHECK("k_resample_tiles");
+        ZM_LAUNCH_PDL("k_resample_tiles", k_resample_tiles, dim3(tl->n, (nc + TILE_IPC - 1) / TILE_IPC),
+                      dim3(TILE_THREADS), smem, st, tp);
     }
     return ZM_OK;
 }
