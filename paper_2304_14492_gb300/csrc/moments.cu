@@ -705,16 +705,18 @@ int launch_stage_spectra(zm_plan_t p, const zm_image_t* imgs, const float* fhat_
     return launch_spectra(p, imgs, fhat_in, batch, (float*)p->ws_F.ptr, fhat_out, false, st);
 }
 
-// Stage 2: the radial projection of the spectra stage 1 left in the workspace.
-int launch_stage_project(zm_plan_t p, int batch, float* out, unsigned flags, cudaStream_t st) {
-    if (blocked_projection(p)) return launch_projection_blocked(p, (const uint8_t*)p->ws_Fblk.ptr, batch, out, flags, st);
+// Stage 2: the radial projection of the spectra stage 1 left in the workspace
+// (consume: no later call reads them, so the blocked form drops them from L2).
+int launch_stage_project(zm_plan_t p, int batch, float* out, unsigned flags, cudaStream_t st, bool consume = false) {
+    if (blocked_projection(p))
+        return launch_projection_blocked(p, (const uint8_t*)p->ws_Fblk.ptr, batch, out, flags, st, consume);
     return launch_projection(p, (const float*)p->ws_F.ptr, batch, out, flags, st);
 }
 
 int launch_moments(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, int batch, float* out,
                    float* fhat_out, unsigned flags, cudaStream_t st) {
     const int s = launch_stage_spectra(p, imgs, fhat_in, batch, fhat_out, st);
-    return s != ZM_OK ? s : launch_stage_project(p, batch, out, flags, st);
+    return s != ZM_OK ? s : launch_stage_project(p, batch, out, flags, st, true);
 }
 
 }  // namespace zm

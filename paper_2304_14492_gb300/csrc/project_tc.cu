@@ -352,10 +352,18 @@ int launch_projection_tc(zm_plan_t p, const float* F, int batch, float* out, uns
 // side, K_m <= 128 rows) comes from the plan's operand blocks, F (the N side,
 // up to 256 columns) from blocks the ring-FFT kernel wrote, both already in
 // the canonical layout, so each 64-node chunk is four bulk copies into a ring
-// of shared-memory stages; one thread waits for a stage, issues its 4 x 3
-// MMAs and commits them to the stage's "empty" barrier, and refills the stage
-// of the previous chunk once those MMAs have read it.  The epilogue writes
-// the moments (Neumann factor applied) straight into out[b][idx(n, m)].
+// of shared-memory stages.  The A copies of the first stages are issued before
+// the grid-dependency wait (A is the plan's, F the previous kernel's output).
+// One thread waits for a stage, issues its MMAs and commits them to the
+// stage's "empty" barrier; a second thread refills each stage as soon as its
+// MMAs have read it.  At this size an MMA costs about the same whatever its N,
+// so the split products share MMAs: F lo lies right after F hi in a stage, so
+// B = [F hi | F lo] (N = 2 x columns) gives A_hi F_hi and A_hi F_lo at once,
+// and when every order has at most 64 rows A = [A hi; A lo] on M (rows 0..63,
+// 64..127) adds A_lo F_hi (and A_lo F_lo) in the same MMA: one MMA per
+// 16-node step instead of three.  The epilogue adds the column halves and the
+// lo rows (passed through the consumed stages) and writes the moments
+// (Neumann factor applied) straight into out[b][idx(n, m)].
 // With ksplit = 2 the radial range is split between the two CTAs of a
 // cluster (blockIdx.z = 0, 1): rank 1 stores its partial D into a buffer in
 // rank 0's shared memory, and rank 0 adds it to its own after a cluster
@@ -379,6 +387,8 @@ struct BlkParams {
     int buf_off;             // byte offset of rank 0's receive buffer (ksplit = 2)
     int neumann;
     float inv_scale;
+    int discard_f;           // the F blocks are the call's scratch: their L2 lines are dropped once copied
+    int stack;               // K_m <= 64 and 2 NT <= 256: one MMA per k step, A hi and lo stacked on M
 };
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -397,6 +407,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     __shared__ __align__(8) uint64_t empty[8];
     __shared__ uint32_t tslot;
     __shared__ int okflag;
+    __shared__ int mma_done, mma_ok, prod_loaded, prod_ok;
     const int m = blockIdx.x, t = blockIdx.y, z = blockIdx.z;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Km = (p.n_max - m) / 2 + 1;
@@ -405,8 +416,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     const int cg0 = t * 32, cgt = min(32, cg - cg0);
     const int cols_t = min(256, p.ncol - t * 256);
     const int NT = ((cols_t + 15) / 16) * 16;
+    // F lo follows F hi in a stage, so one N = 2 NT MMA reads [F hi | F lo]
+    // and A hi once for both products (D columns NT.. hold A_hi F_lo)
+    const bool comb = 2 * NT <= 256;
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)NT) ncols <<= 1;
+    while (ncols < (uint32_t)(comb ? 2 * NT : NT)) ncols <<= 1;
     // this CTA's chunks of the radial range
     const int per = (p.n_chunks + p.ksplit - 1) / p.ksplit;
     const int c_begin = z * per;
@@ -429,50 +443,69 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (p.ksplit > 1) cluster_sync_all();     // both CTAs of the pair run before any shared memory crosses
-    griddep_wait();                    // the spectra blocks are written, `out` is free
-    griddep_launch();
     const uint32_t tmem = tslot;
     const uint32_t sm0 = smem_u32(sm);
 
+    // a stage holds p.cpc consecutive 64-ring chunks, each as
+    // [A hi: rg KB][A lo: rg KB][F hi: bg KB][F lo: bg KB], or, stacked,
+    // [A hi: rg KB, padded to 8 KB][A lo: rg KB][F hi][F lo]; the M = 128 MMA
+    // reads 16 KB from an A base, past rg KB into whatever follows (a 16 KB
+    // pad after the last stage keeps that inside the allocation): those rows
+    // only feed D rows >= K_m (of each half, stacked), which are never read
+    const int bg = NT / 8;
+    const uint32_t a_bytes = (uint32_t)rg * 1024u, b_bytes = (uint32_t)bg * 1024u;
+    const uint32_t a_lo_off = p.stack ? 8192u : a_bytes;
+    const uint32_t sub_bytes = a_lo_off + a_bytes + 2u * b_bytes;
+    const int cpc = p.cpc;
+    const uint32_t stage_bytes = cpc * sub_bytes;
+    const size_t a_chunk = (size_t)rg * 1024;
+    const uint8_t* a_src = p.Ablk + p.ablk_off[m] + (size_t)c_begin * a_chunk;
+    const size_t f_chunk = (size_t)cg * 1024;
+    const uint8_t* f_src = p.Fblk + (((size_t)m * p.n_chunks + c_begin) * cg + cg0) * 1024;
+    const int nst = (nch + cpc - 1) / cpc;            // stage loads (groups of chunks)
+    const int npre = min(nst, S);                     // stages loaded before the first MMA
+    auto subs = [&](int c) { return min(cpc, nch - c * cpc); };
+    // stage load, in two parts: the barrier's byte count and the A copies
+    // (plan constants), then the F copies (the previous kernel's output)
+    auto load_a = [&](int c) {
+        const int st = c % S;
+        const uint32_t base = sm0 + (uint32_t)st * stage_bytes;
+        const uint32_t bar = smem_u32(&full[st]);
+        const int ns = subs(c);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)ns * 2u * (a_bytes + (uint32_t)cgt * 1024u))
+                     : "memory");
+        for (int j = 0; j < ns; ++j) {
+            const size_t ch = (size_t)c * cpc + j;
+            const uint32_t d = base + j * sub_bytes;
+            bulk_copy(d, a_src + ch * a_chunk, a_bytes, bar);
+            bulk_copy(d + a_lo_off, a_src + p.ablk_half + ch * a_chunk, a_bytes, bar);
+        }
+    };
+    auto load_f = [&](int c) {
+        const int st = c % S;
+        const uint32_t base = sm0 + (uint32_t)st * stage_bytes;
+        const uint32_t bar = smem_u32(&full[st]);
+        const int ns = subs(c);
+        for (int j = 0; j < ns; ++j) {
+            const size_t ch = (size_t)c * cpc + j;
+            const uint32_t d = base + j * sub_bytes;
+            bulk_copy(d + a_lo_off + a_bytes, f_src + ch * f_chunk, (uint32_t)cgt * 1024, bar);
+            bulk_copy(d + a_lo_off + a_bytes + b_bytes, f_src + p.fblk_half + ch * f_chunk, (uint32_t)cgt * 1024, bar);
+        }
+    };
+    // the first stages' A blocks are in flight while the previous kernel finishes
+    if (tid == 0)
+        for (int c = 0; c < npre; ++c) load_a(c);
+    griddep_wait();                    // the spectra blocks are written, `out` is free
+    griddep_launch();
+
     if (tid == 0) {
-        // a stage holds p.cpc consecutive 64-ring chunks, each as
-        // [A hi: rg KB][A lo: rg KB][F hi: bg KB][F lo: bg KB]; the M = 128 MMA
-        // reads 16 KB from each A half, past rg KB into whatever follows (a
-        // 16 KB pad after the last stage keeps that inside the allocation):
-        // those rows only feed D rows >= K_m, which are never read
-        const int bg = NT / 8;
-        const uint32_t a_bytes = (uint32_t)rg * 1024u, b_bytes = (uint32_t)bg * 1024u;
-        const uint32_t sub_bytes = 2u * (a_bytes + b_bytes);
-        const int cpc = p.cpc;
-        const uint32_t stage_bytes = cpc * sub_bytes;
-        const size_t a_chunk = (size_t)rg * 1024;
-        const uint8_t* a_src = p.Ablk + p.ablk_off[m] + (size_t)c_begin * a_chunk;
-        const size_t f_chunk = (size_t)cg * 1024;
-        const uint8_t* f_src = p.Fblk + (((size_t)m * p.n_chunks + c_begin) * cg + cg0) * 1024;
-        const int nst = (nch + cpc - 1) / cpc;            // stage loads (groups of chunks)
-        auto subs = [&](int c) { return min(cpc, nch - c * cpc); };
-        auto load = [&](int c) {
-            const int st = c % S;
-            const uint32_t base = sm0 + (uint32_t)st * stage_bytes;
-            const uint32_t bar = smem_u32(&full[st]);
-            const int ns = subs(c);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                         "r"((uint32_t)ns * 2u * (a_bytes + (uint32_t)cgt * 1024u))
-                         : "memory");
-            for (int j = 0; j < ns; ++j) {
-                const size_t ch = (size_t)c * cpc + j;
-                const uint32_t d = base + j * sub_bytes;
-                bulk_copy(d, a_src + ch * a_chunk, a_bytes, bar);
-                bulk_copy(d + a_bytes, a_src + p.ablk_half + ch * a_chunk, a_bytes, bar);
-                bulk_copy(d + 2 * a_bytes, f_src + ch * f_chunk, (uint32_t)cgt * 1024, bar);
-                bulk_copy(d + 2 * a_bytes + b_bytes, f_src + p.fblk_half + ch * f_chunk, (uint32_t)cgt * 1024, bar);
-            }
-        };
-        const uint32_t idesc = instr_desc(NT, 0);
+        const uint32_t idesc = instr_desc(NT, 0), idesc2 = instr_desc(2 * NT, 0);
         const unsigned long long t0 = global_ns();
-        int loaded = 0, done = 0;
+        int done = 0;
         bool ok = true;
-        for (; loaded < nst && loaded < S; ++loaded) load(loaded);
+        for (int c = 0; c < npre; ++c) load_f(c);
         for (int c = 0; c < nst && ok; ++c) {
             const int st = c % S;
             if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c / S) & 1), t0)) {
@@ -482,22 +515,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
             const int ns = subs(c);
             for (int j = 0; j < ns; ++j) {
                 const uint32_t base = sm0 + (uint32_t)st * stage_bytes + j * sub_bytes;
-                const uint32_t ah = base, al = base + a_bytes;
-                const uint32_t fh = base + 2 * a_bytes, fl = fh + b_bytes;
+                const uint32_t ah = base, al = base + a_lo_off;
+                const uint32_t fh = al + a_bytes, fl = fh + b_bytes;
 #pragma unroll
                 for (int ks = 0; ks < TC_KC / 16; ++ks) {
                     const uint32_t off = ks * 256;      // 16 k = two core matrices along K
                     const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
                     const uint64_t dfh = smem_desc(fh + off), dfl = smem_desc(fl + off);
                     const uint32_t acc0 = (c == 0 && j == 0 && ks == 0) ? 0u : 1u;
+                    if (p.stack) {
+                        // [A hi; A lo] x [F hi | F lo]: all four products in one MMA
+                        asm volatile(
+                            "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                            "l"(dah), "l"(dfh), "r"(idesc2), "r"(acc0));
+                        continue;
+                    }
                     asm volatile(
                         "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                        "l"(dah), "l"(dfh), "r"(idesc), "r"(acc0));
-                    asm volatile(
-                        "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                        "l"(dah), "l"(dfl), "r"(idesc), "r"(1u));
+                        "l"(dah), "l"(dfh), "r"(comb ? idesc2 : idesc), "r"(acc0));
+                    if (!comb)
+                        asm volatile(
+                            "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                            "l"(dah), "l"(dfl), "r"(idesc), "r"(1u));
                     asm volatile(
                         "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
@@ -508,32 +550,61 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
                              smem_u32(&empty[st]))
                          : "memory");
             done = c + 1;
-            // refill the stage of the previous group once its MMAs have read it
-            if (c >= 1 && loaded < nst) {
-                const int pc = c - 1, ps = pc % S;
-                if (!mbar_wait(smem_u32(&empty[ps]), (uint32_t)((pc / S) & 1), t0)) {
-                    ok = false;
-                    break;
-                }
-                load(loaded++);
-            }
         }
         if (ok) ok = mbar_wait(smem_u32(&empty[(nst - 1) % S]), (uint32_t)(((nst - 1) / S) & 1), t0);
-        if (!ok) {
-            // a wait ran out: report it, then give the copies and MMAs in flight a
-            // bounded time to land before the shared memory and TMEM are released
-            atomicExch(p.status, ZM_ETIMEOUT);
-            const unsigned long long t1 = global_ns();
-            for (int c = done; c < loaded; ++c) mbar_wait(smem_u32(&full[c % S]), (uint32_t)((c / S) & 1), t1);
-            if (done > 0) mbar_wait(smem_u32(&empty[(done - 1) % S]), (uint32_t)(((done - 1) / S) & 1), t1);
-            okflag = 0;
+        mma_done = done;
+        mma_ok = ok ? 1 : 0;
+    } else if (tid == 32) {
+        // the refills: stage k is loaded as soon as the MMAs of stage k - S
+        // have read its buffer
+        const unsigned long long t0 = global_ns();
+        int k = npre;
+        bool ok = true;
+        for (; k < nst; ++k) {
+            if (!mbar_wait(smem_u32(&empty[k % S]), (uint32_t)(((k - S) / S) & 1), t0)) {
+                ok = false;
+                break;
+            }
+            load_a(k);
+            load_f(k);
         }
+        prod_loaded = k;
+        prod_ok = ok ? 1 : 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (tid == 0 && !(mma_ok && prod_ok)) {
+        // a wait ran out: report it, then give the copies and MMAs in flight a
+        // bounded time to land before the shared memory and TMEM are released
+        atomicExch(p.status, ZM_ETIMEOUT);
+        const unsigned long long t1 = global_ns();
+        for (int c = mma_done; c < prod_loaded; ++c) mbar_wait(smem_u32(&full[c % S]), (uint32_t)((c / S) & 1), t1);
+        if (mma_done > 0)
+            mbar_wait(smem_u32(&empty[(mma_done - 1) % S]), (uint32_t)(((mma_done - 1) / S) & 1), t1);
+        okflag = 0;
+    }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
+    // every F block of this CTA is in shared memory and read by its MMAs: a
+    // scratch copy is dead, so its L2 lines are dropped without a write-back
+    // (each (m, chunk, column group) block is read by this CTA alone).  The
+    // drops take a while; stacked, they wait until after the pair's exchange
+    // and go to the warps with nothing left to do
+    auto discard_f = [&](int t0, int nt) {
+        const int lines = cgt * 8;                     // 128-byte lines per chunk and half
+        for (int e = t0; e < nch * 2 * lines; e += nt) {
+            const int ch = e / (2 * lines), r = e - ch * 2 * lines;
+            const uint8_t* a =
+                f_src + (size_t)ch * f_chunk + (r >= lines ? p.fblk_half : 0) + (size_t)(r % lines) * 128;
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+        }
+    };
+    if (p.discard_f && okflag && !p.stack) discard_f(tid, TC_THREADS);
+
     // epilogue: TMEM lane = row n_local of D (warp w owns lanes 32w..32w+31)
+    // TMEM loads of this warp's 32 lanes, 16 columns each; the values are
+    // usable after tmem_wait (whose operands tie them to the wait)
     auto tmem_ld16 = [&](int c0, uint32_t (&r)[16]) {
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
         asm volatile(
@@ -541,11 +612,71 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    };
+    auto tmem_wait = [&](uint32_t (&r)[16]) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                       "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                       "+r"(r[14]), "+r"(r[15])
+                     :
+                     : "memory");
+    };
+    auto tmem_hold = [&](uint32_t (&r)[16]) {     // orders r after the preceding wait
+        asm volatile(""
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                       "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                       "+r"(r[14]), "+r"(r[15])
+                     :
+                     : "memory");
+    };
+    // columns c0.. of D, plus (two-column-block form) the A_hi F_lo columns
+    // NT + c0.., both loads under one wait
+    auto ld_pair16 = [&](int c0, uint32_t (&r)[16]) {
+        tmem_ld16(c0, r);
+        if (comb) {
+            uint32_t q[16];
+            tmem_ld16(NT + c0, q);
+            tmem_wait(r);
+            tmem_hold(q);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(q[j]));
+        } else {
+            tmem_wait(r);
+        }
     };
     const int nl = warp * 32 + lane;
     const int bstride = NT + 4;                       // floats per buffer row (16-byte rows, conflict-free)
     const uint32_t buf = sm0 + (uint32_t)p.buf_off;   // rank 0's receive buffer [row][bstride]
+    // stacked: D rows 64 + n hold the A_lo products of row n; the warps that
+    // hold them pass their sums on through the consumed stages, [row][bstride]
+    float* xb = reinterpret_cast<float*>(sm);
+    if (p.stack) {
+        if (okflag && warp >= 2 && (warp - 2) * 32 < Km) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // after the MMAs' operand reads
+            float* row = xb + (nl - 64) * bstride;
+            for (int c0 = 0; c0 < NT; c0 += 16) {
+                uint32_t r[16];
+                ld_pair16(c0, r);
+                if (nl - 64 < Km) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(row + c0 + j) =
+                            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                        __uint_as_float(r[j + 3]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // the value of D row nl (nl < K_m): its column halves, and stacked, the A_lo row
+    auto row16 = [&](int c0, uint32_t (&r)[16]) {
+        ld_pair16(c0, r);
+        if (p.stack) {
+            const float* q = xb + nl * bstride + c0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + q[j]);
+        }
+    };
     if (p.ksplit > 1) {
         // tcgen05.ld is warp-wide: the condition is uniform per warp, the
         // stores are per row
@@ -554,7 +685,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
             const uint32_t dst = cluster_map(buf + (uint32_t)(nl * bstride) * 4u, 0);
             for (int c0 = 0; c0 < NT; c0 += 16) {
                 uint32_t r[16];
-                tmem_ld16(c0, r);
+                row16(c0, r);
                 if (nl < Km) {
 #pragma unroll
                     for (int j = 0; j < 16; j += 4)
@@ -564,18 +695,41 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
                                      : "memory");
                 }
             }
+        } else if (z == 0 && okflag && p.stack && warp * 32 < Km) {
+            // meanwhile rank 0 puts its own rows, complete, in place of its A_lo rows
+            for (int c0 = 0; c0 < NT; c0 += 16) {
+                uint32_t r[16];
+                row16(c0, r);
+                if (nl < Km) {
+                    float* q = xb + nl * bstride + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(q + j) = make_float4(
+                            __uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                            __uint_as_float(r[j + 3]));
+                }
+            }
         }
         __syncwarp();
         cluster_sync_all();                           // rank 1's rows are in rank 0's buffer
     }
+    const bool own_in_xb = p.ksplit > 1 && p.stack;   // rank 0's rows are in xb already
+    if (p.stack && p.discard_f && okflag && (z == 1 || warp >= 2))
+        discard_f(z == 1 ? tid : tid - 64, z == 1 ? TC_THREADS : TC_THREADS - 64);
     if (okflag && z == 0 && warp * 32 < Km) {
         const bool live = nl < Km;
         const int idx = live ? moment_index(m + 2 * nl, m) : 0;
         const float f = p.inv_scale * ((p.neumann && m == 0) ? 0.5f : 1.f);
         const float* bufp = reinterpret_cast<const float*>(sm + p.buf_off) + nl * bstride;
+        const bool v2 = ((uintptr_t)p.out & 7u) == 0;   // (re, im) pairs as one 8-byte store
         for (int c0 = 0; c0 < NT; c0 += 16) {
             uint32_t r[16];
-            tmem_ld16(c0, r);
+            if (own_in_xb) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(xb[nl * bstride + c0 + j]);
+            } else {
+                row16(c0, r);
+            }
             if (live) {
                 float v[16];
 #pragma unroll
@@ -590,10 +744,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_project_blk(const __grid_constan
                         v[j + 3] += q.w;
                     }
                 }
+                if (v2) {
+                    // columns come in (re, im) pairs of one image: col even, cols_t even
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = t * 256 + c0 + j;
-                    if (c0 + j < cols_t) p.out[((size_t)(col >> 1) * p.P + idx) * 2 + (col & 1)] = v[j] * f;
+                    for (int j = 0; j < 16; j += 2) {
+                        const int col = t * 256 + c0 + j;
+                        if (c0 + j < cols_t)
+                            *reinterpret_cast<float2*>(p.out + ((size_t)(col >> 1) * p.P + idx) * 2) =
+                                make_float2(v[j] * f, v[j + 1] * f);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = t * 256 + c0 + j;
+                        if (c0 + j < cols_t) p.out[((size_t)(col >> 1) * p.P + idx) * 2 + (col & 1)] = v[j] * f;
+                    }
                 }
             }
         }
@@ -658,7 +823,7 @@ int build_tc_blocks(zm_plan_t p) {
 bool blocked_projection(zm_plan_t p) { return p->Ablk != nullptr; }
 
 int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float* out, unsigned flags,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool consume) {
     const int ncol = 2 * batch;
     const int tiles = (ncol + 255) / 256;
     const int nt_max = ((std::min(ncol, 256) + 15) / 16) * 16;
@@ -674,10 +839,14 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
     bp.n_chunks = p->n_chunks;
     bp.ncol = ncol;
     bp.P = p->P;
-    // chunks per stage: the most (measured: fewer, larger copies pay) that
+    // chunks per stage: the most (measured: fewer, larger copies pay; one
+    // chunk in each of four stages was slower than two in each of two) that
     // still leave room for two stages within `cap` bytes after `tail`
     const int rg_max = (p->n_max / 2 + 1 + 7) / 8;
-    auto stage_bytes = [&](int c) { return c * 2 * (rg_max + nt_max / 8) * 1024; };
+    // A hi and lo stacked on the MMA's M (rows 0..63 and 64..127) when every
+    // order has at most 64 rows and [F hi | F lo] fits one MMA's N
+    const bool stack = rg_max <= 8 && 2 * nt_max <= 256;
+    auto stage_bytes = [&](int c) { return c * ((stack ? 8 + rg_max : 2 * rg_max) + 2 * (nt_max / 8)) * 1024; };
     auto fit = [&](int cap, int tail, int* cpc, int* stages) {
         const int budget = cap - tail;
         int c = BLK_CPC_MAX;
@@ -704,6 +873,12 @@ int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float
     bp.buf_off = stages * stage_bytes(cpc);
     bp.neumann = (flags & ZM_NEUMANN) ? 1 : 0;
     bp.inv_scale = 1.0f / p->a_scale;
+    bp.discard_f = consume && ((uintptr_t)Fblk & 127u) == 0 && bp.fblk_half % 128 == 0 ? 1 : 0;
+    // the epilogue's rows (64 x (nt_max + 4) floats: the A_lo rows, then rank
+    // 0's own rows) go through the stages of the smallest order (rg = 1),
+    // which always hold them
+    bp.stack = stack && (size_t)bp.stages * bp.cpc * (9 + 2 * (nt_max / 8)) * 1024 >= (size_t)64 * (nt_max + 4) * 4
+                   ? 1 : 0;
     const size_t smem = (size_t)bp.buf_off + (split ? tail2 : BLK_A_BYTES);
     static size_t configured[64] = {0};
     const int dev = p->device;

@@ -240,8 +240,9 @@ int launch_moments(zm_plan_t p, const zm_image_t* imgs, const float* fhat_in, in
 // Blocked tensor-core projection (project_tc.cu).
 int build_tc_blocks(zm_plan_t p);
 bool blocked_projection(zm_plan_t p);
+// consume: the blocks are scratch of this call (zm_moments), dropped from L2 once read
 int launch_projection_blocked(zm_plan_t p, const uint8_t* Fblk, int batch, float* out, unsigned flags,
-                              cudaStream_t st);
+                              cudaStream_t st, bool consume = false);
 // Tensor-core radial reconstruction (recon_tc.cu), bf16 plans.
 int build_recon_blocks(zm_plan_t p);
 int launch_radial_tc(zm_plan_t p, const float* moments, int batch, unsigned flags, float* G, cudaStream_t st);
