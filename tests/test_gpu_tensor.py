@@ -72,8 +72,8 @@ def run(n_max, n_rho, n_theta, flags, imgs, call_flags=0):
     (20, 32, 64, (64, 64), 1),          # small plan, one column tile
     (50, 256, 256, (512, 512), 16),     # 32 columns
     (13, 37, 32, (45, 70), 70),         # ragged N_rho, 140 columns -> 2 column tiles
-    (126, 40, 64, (50, 50), 3),         # K_0 = 64: the largest orders with A hi / lo stacked on M
-    (200, 64, 128, (96, 96), 5),        # K_0 = 101: F hi / lo share MMAs, A hi / lo do not
+    (126, 40, 256, (50, 50), 3),        # K_0 = 64: the largest orders with A hi / lo stacked on M
+    (200, 64, 512, (96, 96), 5),        # K_0 = 101: F hi / lo share MMAs, A hi / lo do not
     (300, 24, 1024, (48, 48), 3),       # K_0 = 151 -> N = 160 (256 TMEM columns)
     (600, 8, 2048, (16, 16), 2),        # K_0 = 301 -> two order tiles
     (0, 5, 8, (10, 10), 1),             # single moment
