@@ -204,8 +204,12 @@ __global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_spectra(cons
 // FFT has left the registers), splits each into F_m, m <= n_max, and stages
 // them as Fs[image][re/im][ring][m]; then 8 consecutive threads write one
 // full 128-byte line (8 columns x 8 rings) per order and half.
+// Occupancy: three CTAs per SM at N = 1024 (shared memory, 69 KB each), so the
+// register bound is set for three (77 registers; at 64 for four the kernel was
+// 0.7 us per batch of 16 4K frames slower).
 template <int LOGN>
-__global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : 4)) k_ring_blk(const __grid_constant__ KbParams p) {
+__global__ void __launch_bounds__(256, (LOGN >= 11 ? 2 : (LOGN == 10 ? 3 : 4)))
+    k_ring_blk(const __grid_constant__ KbParams p) {
     using FFT = RingFFT<LOGN>;
     constexpr int N = FFT::N;
     constexpr int ROW = FFT::ROW_FLOATS;
