@@ -45,6 +45,8 @@ def split_moments(a, f, p, lo_bits=None, terms_kept=("hh", "hl", "lh")):
         z += np.sum(ah * fl, axis=1)
     if "lh" in terms_kept:
         z += np.sum(al * fh, axis=1)
+    if "ll" in terms_kept:
+        z += np.sum(al * fl, axis=1)
     return z
 
 

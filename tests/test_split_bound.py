@@ -18,7 +18,9 @@ rounding of the accumulation.  The products here are emulated exactly (float64
 holds every product of two 16-bit values and their short sums), so the test
 sees the split alone: the bf16 and fp16 splits stay inside the bound on the
 64x64 and 512x512 workloads, and splits that keep less (a shorter lo part, a
-dropped cross term, no lo part) break it, so the bound detects them.
+dropped cross term, no lo part) break it, so the bound detects them.  The
+stacked form of the projection, which also forms a_lo f_lo, has the tighter
+bound (2 u^2 + u^4) S_nm, checked the same way.
 """
 
 import numpy as np
@@ -62,6 +64,22 @@ def test_weaker_bf16_splits_break_the_bound(workload, weaker):
     a, f, z, S = workload
     err = np.abs(split_moments(a, f, 8, **weaker) - z)
     assert np.max(err / (3 * 2.0 ** -18 * S)) > 1.0
+
+
+# When every order has at most 64 rows the blocked projection stacks A hi and
+# A lo on the MMA's M and multiplies both by [F hi | F lo], so it also forms
+# a_lo f_lo.  With e_a = a - a_hi - a_lo and e_f = f - f_hi - f_lo,
+#     a f - (a_hi + a_lo)(f_hi + f_lo) = a e_f + e_a f - e_a e_f,
+# so the four products are off by at most (2 u^2 + u^4) |a f| per term, a
+# bound inside the three-product one (the errors themselves need not shrink
+# term by term: rounding errors of the three-product form can cancel).
+@pytest.mark.parametrize("p", [8, 11])
+def test_four_product_split_stays_inside_its_tighter_bound(workload, p):
+    a, f, z, S = workload
+    u2 = 2.0 ** (-2 * p)
+    err4 = np.abs(split_moments(a, f, p, terms_kept=("hh", "hl", "lh", "ll")) - z)
+    assert np.all(err4 <= (2 * u2 + u2 * u2) * S), float(np.max(err4 / ((2 * u2 + u2 * u2) * S)))
+    assert np.all(err4 <= 3 * u2 * S)
 
 
 # ---- the angular sums as a split product (the tensor-core DFT kernel)
