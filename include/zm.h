@@ -278,9 +278,12 @@ int zm_project_noalloc(zm_plan_t plan, const float* spectra, int batch, float* o
  * float[batch][P][2].  zm_moments gives the same moments as the two calls in
  * turn.  Use them to time or overlap the stages; the spectra stay in the plan
  * until the next call that computes spectra with this plan, so calls on one
- * plan must not overlap on the GPU.  zm_stage_project returns ZM_EINVAL if
- * `batch` differs from the last zm_stage_spectra's.  Asynchronous on
- * `stream`; zm_stage_spectra may grow the workspace (cudaMalloc). */
+ * plan must not overlap on the GPU.  Such a call in between (zm_moments and
+ * its variants use the same workspace, and zm_moments drops its spectra from
+ * L2 once projected) leaves zm_stage_project with undefined values until the
+ * next zm_stage_spectra.  zm_stage_project returns ZM_EINVAL if `batch`
+ * differs from the last zm_stage_spectra's.  Asynchronous on `stream`;
+ * zm_stage_spectra may grow the workspace (cudaMalloc). */
 int zm_stage_spectra(zm_plan_t plan, const zm_image_t* imgs, int batch, void* stream);
 int zm_stage_project(zm_plan_t plan, int batch, float* out, unsigned flags, void* stream);
 
